@@ -1,0 +1,171 @@
+/*
+ * ttv.h -- C ABI of the GB300 (sm_103a) sparse tensor-times-vector library.
+ *
+ * The operation (paper Sec. 3.3, Eq. 3 and the multi-vector paragraph before
+ * it): a d-way sparse COO tensor A (int64 subscripts, one value per nonzero)
+ * is multiplied by n_v dense vectors x_m, one for each contracted mode m in S.
+ * The result has order d - n_v over the surviving modes R = [0,d) \ S, taken
+ * in increasing order:
+ *
+ *     B(i_R) = sum_{k : subs[k,R] == i_R}  vals[k] * prod_{m in S} x_m[subs[k,m]]
+ *
+ * Conventions shared by every entry point:
+ *   - Indices are 0-based (the paper counts from 1; its "mode k = 2" is mode 1).
+ *   - Device pointers are plain CUDA device addresses (for example from torch);
+ *     the library never takes ownership of inputs.  Host arrays (shape, modes,
+ *     the array of vector pointers) are read during the call only.
+ *   - A sparse result is canonical COO: one entry per distinct surviving
+ *     subscript tuple that occurs in the input (even when its sum is zero),
+ *     in ascending lexicographic order of the tuple -- the row order of the
+ *     "unique" step the paper describes for pyttb's sptensor.ttv (Sec. 3.3).
+ *     Duplicate input subscripts are summed.
+ *   - A dense result is a row-major array over shape[R] (last mode fastest).
+ *     n_v == d gives an order-0 result: one scalar (nnz 1).
+ *   - Calls are asynchronous on `stream` except where stated: unless
+ *     opts->async is set, the call synchronises `stream` once at the end to
+ *     read the output count and the error word, so out->nnz and the return
+ *     code are final on return.
+ *   - Return value: TTV_OK (0) or a negative TTV_ERR_*; ttv_last_error()
+ *     gives a message for the calling thread's last failure.
+ *   - Subscript bounds are checked inside the streaming kernel at no extra
+ *     traffic: an out-of-range subscript is skipped and reported as
+ *     TTV_ERR_SUBSCRIPT; the output contents are then unspecified.
+ */
+#ifndef TTV_GB300_H
+#define TTV_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TTV_MAX_D 8              /* largest tensor order the kernels accept */
+
+typedef struct CUstream_st *ttv_stream_t;   /* same handle as cudaStream_t; NULL = default stream */
+
+enum {
+    TTV_OK = 0,
+    TTV_ERR_ARG = -1,            /* null pointer, bad size, bad enum value          */
+    TTV_ERR_MODE = -2,           /* contracted mode out of range or repeated        */
+    TTV_ERR_VEC_LEN = -3,        /* vector length differs from shape[mode]          */
+    TTV_ERR_SUBSCRIPT = -4,      /* a subscript outside [0, shape[m]) (device check)*/
+    TTV_ERR_KEY_OVERFLOW = -5,   /* prod(shape[R]) does not fit in 64 bits          */
+    TTV_ERR_BUDGET = -6,         /* workspace or server memory budget too small     */
+    TTV_ERR_TIMEOUT = -7,        /* a bounded device wait or a server wait ran out  */
+    TTV_ERR_CUDA = -8,           /* a CUDA runtime call failed                      */
+    TTV_ERR_CAPACITY = -9,       /* caller-provided output buffer too small         */
+    TTV_ERR_NOMEM = -10,         /* allocation failed                               */
+    TTV_ERR_UNSUPPORTED = -11,   /* combination not implemented                     */
+};
+
+typedef enum { TTV_F64 = 0, TTV_F32 = 1 } ttv_dtype;
+
+typedef enum {
+    TTV_OUT_SPARSE = 0,          /* canonical COO (default)                          */
+    TTV_OUT_DENSE = 1,           /* dense row-major array over shape[R]              */
+    TTV_OUT_AUTO = 2             /* dense when nnz_out > 0.5 * prod(shape[R]): the
+                                    pyttb conversion rule the paper mentions (Sec. 3.3) */
+} ttv_out_format;
+
+typedef enum {
+    TTV_PATH_AUTO = 0,           /* planner / autotuner choice                        */
+    TTV_PATH_DENSE = 1,          /* block-private dense accumulator (small prod R)    */
+    TTV_PATH_SORT = 2,           /* LSD onesweep radix sort + segmented reduction     */
+    TTV_PATH_HASH = 3,           /* warp-aggregated HBM hash table + compaction       */
+    TTV_PATH_BUCKET = 4          /* splitter partition + in-shared-memory sort        */
+} ttv_path;
+
+typedef enum {
+    TTV_ACCUM_FP64 = 0,          /* IEEE binary64 additions                           */
+    TTV_ACCUM_COMPENSATED = 1,   /* binary64 with two-sum error compensation          */
+} ttv_accum;
+
+/* Input tensor.  subs[k * stride_nz + m * stride_mode] is subscript m of
+ * nonzero k: (stride_nz, stride_mode) = (d, 1) for row-major nnz x d (AoS) or
+ * (1, nnz) for one contiguous column per mode (SoA, pyttb's column-major
+ * layout, paper Sec. 3.2).  Strides are in elements. */
+typedef struct {
+    const int64_t *subs;         /* device */
+    int64_t stride_nz;
+    int64_t stride_mode;
+    const void *vals;            /* device, nnz values of val_dtype               */
+    ttv_dtype val_dtype;
+    int64_t nnz;                 /* >= 0                                          */
+    const int64_t *shape;        /* host, d sizes >= 1                            */
+    int32_t d;                   /* 1 .. TTV_MAX_D                                */
+} ttv_tensor;
+
+/* Result.  Before the call the caller either sets subs/vals to NULL (the
+ * library allocates them; release with ttv_out_free) or points them at device
+ * buffers of subs_capacity x order int64 (row-major) and vals_capacity values
+ * (the library writes into them and ttv_out_free leaves them alone).  A safe
+ * capacity is ttv_out_capacity(); a smaller one that the result does not fit
+ * gives TTV_ERR_CAPACITY.  After the call: order, shape, nnz (valid on return
+ * unless opts->async), is_dense, dtype (always TTV_F64 values). */
+typedef struct {
+    int32_t order;
+    int64_t shape[TTV_MAX_D];
+    int64_t nnz;                 /* output entries; prod(shape) when dense          */
+    int64_t *subs;               /* nnz x order row-major; unused when dense        */
+    void *vals;                  /* nnz values                                      */
+    int64_t subs_capacity;       /* rows available at subs (caller buffers)         */
+    int64_t vals_capacity;       /* values available at vals (caller buffers)       */
+    ttv_dtype dtype;
+    int32_t is_dense;
+    void *internal;              /* library bookkeeping; zero-initialise            */
+} ttv_out;
+
+typedef struct {
+    int32_t fmt;                 /* ttv_out_format                                  */
+    int32_t path;                /* ttv_path                                        */
+    int32_t accum;               /* ttv_accum                                       */
+    int32_t deterministic;       /* nonzero: bit-identical results run to run       */
+    int32_t async;               /* nonzero: do not synchronise; call ttv_out_sync  */
+    void *workspace;             /* device scratch, or NULL to let the library
+                                    allocate from its stream-ordered pool          */
+    size_t workspace_bytes;
+} ttv_opts;
+
+/* Defaults: SPARSE, AUTO path, FP64, deterministic, synchronous, own workspace. */
+void ttv_opts_init(ttv_opts *opts);
+
+/* Single-vector TTV, A x_mode v (paper Eq. 3).  v is a device vector of
+ * shape[mode] entries of v_dtype.  Result order d - 1. */
+int ttv_single(const ttv_tensor *t, int32_t mode, const void *v, ttv_dtype v_dtype,
+               ttv_out *out, const ttv_opts *opts, ttv_stream_t stream);
+
+/* Multi-vector TTV (paper Sec. 3.3, n_v in {1..d}): vecs[i] multiplies mode
+ * modes[i]; modes are distinct, in any order (the result does not depend on
+ * it).  n_v == d - 1 is the all-but-one form; n_v == d gives a scalar. */
+int ttv_multi(const ttv_tensor *t, const int32_t *modes, int32_t n_v,
+              const void *const *vecs, ttv_dtype v_dtype,
+              ttv_out *out, const ttv_opts *opts, ttv_stream_t stream);
+
+/* Upper bounds for caller-allocated results: rows of subs and number of
+ * values.  Sparse: min(nnz, prod shape[R]) (at least 1 for order 0).
+ * Dense: prod shape[R]. */
+int ttv_out_capacity(const ttv_tensor *t, const int32_t *modes, int32_t n_v,
+                     const ttv_opts *opts, int64_t *rows, int64_t *values);
+
+/* Device scratch a ttv_multi call with these arguments needs when the caller
+ * supplies opts->workspace. */
+int ttv_workspace_size(const ttv_tensor *t, const int32_t *modes, int32_t n_v,
+                       ttv_dtype v_dtype, const ttv_opts *opts, size_t *bytes);
+
+/* Completes an opts->async call: synchronises its stream, fills out->nnz and
+ * returns the call's device-side status. */
+int ttv_out_sync(ttv_out *out);
+
+/* Releases what the library allocated for `out` (not caller buffers). */
+void ttv_out_free(ttv_out *out);
+
+/* Message for the calling thread's last error ("" if none). */
+const char *ttv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTV_GB300_H */

@@ -1,0 +1,157 @@
+"""CPU oracle for the sparse tensor-times-vector product (paper Sec. 3.3, Eq. 3).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it; the CUDA
+library (``paper_2510_01495_gb300``) neither imports nor links it, and this
+package imports nothing from the library.
+
+``ttv`` wraps the plain C statement in ``ttv_oracle.c`` (built with gcc and
+``-ffp-contract=off``).  It upcasts float32 inputs to float64 exactly before
+the call, so an FP32-stored tensor is evaluated as the exact FP64 values it
+holds.  Parity status of every function here: pinned (see tests/test_oracle_pins.py).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ttv_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "libttv_oracle.so")
+_MAX_D = 16
+_lock = threading.Lock()
+_lib = None
+
+ERRORS = {
+    0: "ok",
+    -1: "invalid argument",
+    -2: "invalid or repeated mode",
+    -3: "vector length differs from the mode size",
+    -4: "subscript out of range",
+    -5: "out of memory",
+}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int):
+        super().__init__(f"oracle_ttv failed: {ERRORS.get(code, code)} ({code})")
+        self.code = code
+
+
+class _Out(ctypes.Structure):
+    _fields_ = [
+        ("order", ctypes.c_int32),
+        ("shape", ctypes.c_int64 * _MAX_D),
+        ("nnz", ctypes.c_int64),
+        ("subs", ctypes.POINTER(ctypes.c_int64)),
+        ("vals", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+def compile_library(src: str = _SRC, out_path: str = _LIB_PATH, extra_flags=()) -> str:
+    """Compile the C oracle into a shared library (plain gcc, no CUDA)."""
+    os.makedirs(os.path.dirname(out_path), exist_ok=True)
+    tmp = out_path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+           *extra_flags, "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True, capture_output=True)
+    os.replace(tmp, out_path)
+    return out_path
+
+
+def build() -> str:
+    """Build the oracle library if it is missing or older than its source."""
+    if (not os.path.exists(_LIB_PATH)
+            or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
+        compile_library()
+    return _LIB_PATH
+
+
+def load_library(path: str):
+    lib = ctypes.CDLL(path)
+    lib.oracle_ttv.restype = ctypes.c_int
+    lib.oracle_ttv.argtypes = [
+        ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+        ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+        ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), ctypes.c_int32,
+        ctypes.POINTER(_Out)]
+    lib.oracle_free.restype = None
+    lib.oracle_free.argtypes = [ctypes.POINTER(_Out)]
+    return lib
+
+
+def _get_lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = load_library(build())
+    return _lib
+
+
+def _as_f64(a) -> np.ndarray:
+    a = np.asarray(a)
+    if a.dtype not in (np.float64, np.float32):
+        raise TypeError(f"values must be float64 or float32, got {a.dtype}")
+    return np.ascontiguousarray(a, dtype=np.float64)   # float32 -> float64 is exact
+
+
+def ttv(subs, vals, shape, modes, vecs, dense: bool = False, lib=None):
+    """Sparse TTV by the plain definition.
+
+    subs  : (nnz, d) integer array of 0-based subscripts (any memory order)
+    vals  : (nnz,) float64 or float32
+    shape : d mode sizes
+    modes : contracted modes (a single int or a sequence), any order
+    vecs  : one vector per entry of ``modes`` (float64 or float32)
+    dense : return a dense array of shape[R] instead of COO
+
+    Returns (newsubs (nnz_out, d - n_v) int64, newvals (nnz_out,) float64,
+    newshape tuple) -- for ``dense`` newsubs is None and newvals has shape
+    newshape (a 0-d array when every mode is contracted).
+    """
+    lib = lib or _get_lib()
+    if np.isscalar(modes):
+        modes, vecs = [int(modes)], [vecs]
+    shape = np.ascontiguousarray(np.asarray(shape, dtype=np.int64).reshape(-1))
+    d = int(shape.size)
+    subs = np.ascontiguousarray(np.asarray(subs, dtype=np.int64).reshape(-1, d))
+    vals = _as_f64(vals).reshape(-1)
+    if subs.shape[0] != vals.shape[0]:
+        raise ValueError("subs and vals disagree on nnz")
+    modes_a = np.ascontiguousarray(np.asarray(modes, dtype=np.int32).reshape(-1))
+    vec_arrs = [_as_f64(v).reshape(-1) for v in vecs]
+    if len(vec_arrs) != modes_a.size:
+        raise ValueError("one vector per contracted mode")
+    lens = np.ascontiguousarray(np.array([v.size for v in vec_arrs], dtype=np.int64))
+    ptr_arr = (ctypes.POINTER(ctypes.c_double) * max(1, len(vec_arrs)))(
+        *[v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for v in vec_arrs])
+    out = _Out()
+    rc = lib.oracle_ttv(
+        d, shape.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(vals.size),
+        subs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        int(modes_a.size), modes_a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+        lens.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ptr_arr,
+        1 if dense else 0, ctypes.byref(out))
+    if rc != 0:
+        raise OracleError(rc)
+    try:
+        order = out.order
+        newshape = tuple(int(out.shape[j]) for j in range(order))
+        n = int(out.nnz)
+        vals_out = np.ctypeslib.as_array(out.vals, shape=(max(n, 1),))[:n].copy()
+        if dense:
+            return None, vals_out.reshape(newshape), newshape
+        if order > 0 and n > 0:
+            subs_out = np.ctypeslib.as_array(out.subs, shape=(n * order,)).copy().reshape(n, order)
+        else:
+            subs_out = np.zeros((n, order), dtype=np.int64)
+        return subs_out, vals_out, newshape
+    finally:
+        lib.oracle_free(ctypes.byref(out))

@@ -1,0 +1,56 @@
+"""The CPU oracle against its pins (no GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle_pins as P
+
+
+@pytest.mark.parametrize("check", P.ALL_CHECKS, ids=lambda c: c.__name__)
+def test_pin(check):
+    check(oracle.ttv)
+
+
+def test_errors():
+    subs = np.array([[0, 1], [1, 0]], dtype=np.int64)
+    vals = np.array([1.0, 2.0])
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.ttv(subs, vals, (2, 2), [2], [np.ones(2)])
+    assert e.value.code == -2
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.ttv(subs, vals, (2, 2), [0, 0], [np.ones(2), np.ones(2)])
+    assert e.value.code == -2
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.ttv(subs, vals, (2, 2), [0], [np.ones(3)])
+    assert e.value.code == -3
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.ttv(np.array([[0, 2]]), np.array([1.0]), (2, 2), [0], [np.ones(2)])
+    assert e.value.code == -4
+
+
+def test_empty_and_scalar():
+    s, v, sh = oracle.ttv(np.zeros((0, 3), np.int64), np.zeros(0), (2, 3, 4), [1], [np.ones(3)])
+    assert sh == (2, 4) and s.shape == (0, 2) and v.shape == (0,)
+    s, v, sh = oracle.ttv(np.zeros((0, 2), np.int64), np.zeros(0), (2, 3), [0, 1], [np.ones(2), np.ones(3)])
+    assert sh == () and list(v) == [0.0]
+    _, dv, sh = oracle.ttv(np.zeros((0, 2), np.int64), np.zeros(0), (2, 3), [0], [np.ones(2)], dense=True)
+    assert sh == (3,) and list(dv) == [0.0, 0.0, 0.0]
+
+
+def test_float32_inputs_are_upcast_exactly():
+    g = np.random.default_rng(3)
+    subs = np.stack([g.integers(0, 5, 40), g.integers(0, 4, 40)], axis=1)
+    v32 = g.uniform(-1, 1, 40).astype(np.float32)
+    x32 = g.uniform(-1, 1, 4).astype(np.float32)
+    a = oracle.ttv(subs, v32, (5, 4), [1], [x32])
+    b = oracle.ttv(subs, v32.astype(np.float64), (5, 4), [1], [x32.astype(np.float64)])
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_duplicates_summed_in_input_order():
+    # 0.1 + 0.2 + 0.3 in one group: compensated sum gives the double nearest the exact sum
+    subs = np.array([[0, 0], [0, 1], [0, 2]], dtype=np.int64)
+    s, v, _ = oracle.ttv(subs, np.array([0.1, 0.2, 0.3]), (1, 3), [1], [np.ones(3)])
+    from fractions import Fraction
+    exact = Fraction(0.1) + Fraction(0.2) + Fraction(0.3)
+    assert v[0] == float(exact)
