@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 sparse TTV library.
+
+One step = one complete TTV (stream, gather, scale, linearise, accumulate,
+emit) of the chosen workload through the library's C ABI.  Default workload:
+the all-but-one-mode TTV (vectors on modes 0, 1, 3) of a 1000^4 tensor with
+1e7 distinct uniform nonzeros, values and vectors U[-1,1], dense length-1000
+result; subscripts stored as d contiguous columns (pyttb's column-major
+layout).  Inputs (400 MB) are larger than L2, so no flush between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+import synthetic as S  # noqa: E402
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+WORKLOADS = {
+    "allbutone_4way_1000": dict(
+        make=lambda dev, seed, nnz=None: S.allbutone_4way_1000(seed=seed, device=dev, nnz=nnz or 10_000_000), fmt="dense",
+        desc="all-but-one TTV, modes 0,1,3 of a 1000^4 COO tensor, nnz 1e7 uniform distinct, U[-1,1], dense 1000 result"),
+    "single_5way_zipf": dict(
+        make=lambda dev, seed, nnz=None: S.single_5way_zipf(seed=seed, device=dev, nnz=nnz or 100_000_000), fmt="sparse",
+        desc="single TTV mode 2 of a 20000x5000x100000x2000x500 COO tensor, nnz 1e8 Zipf(1.2) distinct, N(0,1), sparse 4-way result"),
+    "single_3way_100": dict(
+        make=lambda dev, seed, nnz=None: S.single_3way_100(seed=seed, device=dev), fmt="sparse",
+        desc="single TTV mode 0 of a 100^3 COO tensor, nnz 1e4 uniform distinct, sparse 100x100 result"),
+}
+
+# Kernel whose roofline is reported, per workload, and its algorithmic bytes
+# per launch: every nonzero's d subscripts and value read once, plus the
+# contracted vectors once.
+DOMINANT = {"allbutone_4way_1000": "dense_accum", "single_5way_zipf": "keys_terms", "single_3way_100": "dense_accum"}
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel from an ncu capture, with the sha1 of the kernel sources it was taken
+# on; reported as null once the sources differ.
+TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2510_01495_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(problem, nnz_out: int, w: int = 8) -> dict:
+    """Bytes a TTV must move: subs + vals once, contracted vectors once, and
+    the result (rows of order int64 subscripts plus a value; values only when
+    dense)."""
+    t = problem.tensor
+    d = t.d
+    vec = sum(t.shape[m] for m in problem.modes) * w
+    order = d - len(problem.modes)
+    inp = t.nnz * (8 * d + w)
+    out = nnz_out * (8 * order + 8) if not problem.dense else nnz_out * 8
+    return {"input": inp, "vectors": vec, "output": out, "total": inp + vec + out,
+            "gathered_per_nonzero": t.nnz * len(problem.modes) * w}
+
+
+def cpu_oracle_sample(problem, target_s: float = 10.0, max_nnz: int = 20_000_000):
+    """The CPU oracle on the first m nonzeros of the workload (m chosen so the
+    call runs ~target_s seconds, at most max_nnz); returns GNNZ/s and what was run."""
+    import oracle
+    t = problem.tensor
+    subs = t.subs.cpu().numpy() if t.subs.is_cuda else t.subs.numpy()
+    vals = t.vals.cpu().numpy()
+    vecs = [v.cpu().numpy() for v in problem.vecs]
+    oracle.build()
+    m = min(t.nnz, 200_000)
+    t0 = time.perf_counter()
+    oracle.ttv(subs[:m], vals[:m], t.shape, problem.modes, vecs, dense=problem.dense)
+    dt = time.perf_counter() - t0
+    m2 = int(min(t.nnz, max_nnz, max(m, m * target_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.ttv(subs[:m2], vals[:m2], t.shape, problem.modes, vecs, dense=problem.dense)
+    dt2 = time.perf_counter() - t0
+    return m2 / dt2 / 1e9, m2, dt2
+
+
+def run_reference(args, rank, world):
+    """The oracle, as it stands, on the host cores: each step a bounded sample."""
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    problem = wl["make"]("cpu", args.seed, args.nnz)
+    import oracle
+    oracle.build()
+    t = problem.tensor
+    subs, vals = t.subs.numpy(), t.vals.numpy()
+    vecs = [v.numpy() for v in problem.vecs]
+    m = min(t.nnz, args.ref_sample)
+    for _ in range(args.warmup):
+        oracle.ttv(subs[:m], vals[:m], t.shape, problem.modes, vecs, dense=problem.dense)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.ttv(subs[:m], vals[:m], t.shape, problem.modes, vecs, dense=problem.dense)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = m * args.steps / total / 1e9
+    line = {
+        "impl": "reference", "metric": "TTV nonzeros/sec", "value": value, "unit": "GNNZ/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "layout": "aos", "sample_nnz": m},
+        "cpu_baseline": {"value": value, "unit": "GNNZ/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {m} of {t.nnz} nonzeros per step"},
+        "e2e": {"value": value, "unit": "GNNZ/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="allbutone_4way_1000", choices=sorted(WORKLOADS))
+    ap.add_argument("--path", default="auto")
+    ap.add_argument("--layout", default="soa", choices=["soa", "aos"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--nnz", type=int, default=None, help="smaller case of the workload (profiling)")
+    ap.add_argument("--ref-sample", type=int, default=1_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    if args.seed == 0:
+        args.seed = {"allbutone_4way_1000": 2, "single_5way_zipf": 3, "single_3way_100": 1}[args.workload]
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import paper_2510_01495_gb300 as ttv
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    lib = ttv.load()
+
+    wl = WORKLOADS[args.workload]
+    # independent replica per rank: its own seed, no data-path collective
+    problem = wl["make"](dev, args.seed + 1000 * rank, args.nnz)
+    t = problem.tensor
+    if args.layout == "soa":
+        subs = t.subs.t().contiguous().t()
+    else:
+        subs = t.subs.contiguous()
+    vals = t.vals.contiguous()
+    vecs = [v.contiguous() for v in problem.vecs]
+    fmt = wl["fmt"]
+    del t
+
+    # preallocated workspace and result (the steady-state way to call the ABI)
+    ws_bytes = ttv.workspace_size(subs, vals, problem.tensor.shape, problem.modes, fmt=fmt, path=args.path)
+    workspace = torch.empty(max(1, ws_bytes), dtype=torch.uint8, device=dev)
+    rows, nv = ttv.out_capacity(subs, vals, problem.tensor.shape, problem.modes, fmt=fmt, path=args.path)
+    order = problem.tensor.d - len(problem.modes)
+    out_vals = torch.empty(nv, dtype=torch.float64, device=dev)
+    out_subs = torch.empty((max(1, rows), max(1, order)), dtype=torch.int64, device=dev) if fmt != "dense" else None
+
+    stream = torch.cuda.current_stream(dev)
+    tdesc = ttv.make_tensor(subs, vals, problem.tensor.shape)
+    modes_c = (ctypes.c_int32 * len(problem.modes))(*problem.modes)
+    vecp = (ctypes.c_void_p * len(vecs))(*[v.data_ptr() for v in vecs])
+    lens = (ctypes.c_int64 * len(vecs))(*[v.numel() for v in vecs])
+    opts = ttv.make_opts(fmt=fmt, path=args.path, workspace=workspace, async_=True)
+    sh = ctypes.c_void_p(stream.cuda_stream)
+
+    def submit():
+        res = ttv.Out()
+        res.vals = out_vals.data_ptr()
+        res.vals_capacity = out_vals.numel()
+        if out_subs is not None:
+            res.subs = out_subs.data_ptr()
+            res.subs_capacity = out_subs.shape[0]
+        rc = lib.ttv_multi_checked(ctypes.byref(tdesc), modes_c, len(problem.modes), vecp, lens, 0,
+                                   ctypes.byref(res), ctypes.byref(opts), sh)
+        if rc != 0:
+            raise ttv.TTVError(rc, lib.ttv_last_error().decode())
+        return res
+
+    def finish(results):
+        nnz_out = None
+        for r in results:
+            rc = lib.ttv_out_sync(ctypes.byref(r))
+            if rc != 0:
+                raise ttv.TTVError(rc, lib.ttv_last_error().decode())
+            nnz_out = int(r.nnz)
+            lib.ttv_out_free(ctypes.byref(r))
+        return nnz_out
+
+    for _ in range(args.warmup):
+        nnz_out = finish([submit()])
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: K steps, device resident inputs ----
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    ttv.profile_reset()
+    ttv.profile_enable(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = ttv.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    pending = []
+    for _ in range(args.steps):
+        pending.append(submit())
+        if len(pending) >= 64:
+            finish(pending[:-8])
+            pending = pending[-8:]
+    ev1.record(stream)
+    nnz_out = finish(pending)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    launches = ttv.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    ttv.profile_collect()
+    ttv.profile_enable(False)
+    clk = clocks.stop()
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    nnz = problem.tensor.nnz
+    value = nnz * args.steps * world / (ms * 1e-3) / 1e9
+    ms_step = ms / args.steps
+
+    # ---- per-kernel roofline of the dominant kernel ----
+    peaks, peak_src = load_peaks()
+    per_kernel = {}
+    for name in ttv.profile_names():
+        tot, n = ttv.profile_get(name)
+        per_kernel[name] = {"ms_total": tot, "launches": n, "ms_avg": tot / max(1, n)}
+    dom = DOMINANT[args.workload]
+    if dom not in per_kernel and per_kernel:
+        dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_total"])
+    ab = algorithmic_bytes(problem, nnz_out if fmt != "dense" else int(np.prod([problem.tensor.shape[m] for m in range(problem.tensor.d) if m not in problem.modes])))
+    dom_bytes = ab["input"] + ab["vectors"]
+    dom_ms = per_kernel.get(dom, {}).get("ms_avg", float("nan"))
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms and dom_ms == dom_ms else None
+    peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    src_hash = kernel_source_hash()
+    traffic = None
+    tr = TRAFFIC.get(args.workload)
+    if tr and tr.get("sources") == src_hash and tr.get("kernel") == dom:
+        traffic = tr["bytes_per_launch"]
+
+    line = {
+        "metric": "TTV nonzeros/sec", "value": value, "unit": "GNNZ/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "layout": args.layout, "path": args.path,
+                   "nnz": nnz, "nnz_out": nnz_out, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "peak_source": f"{peak_src} hbm_gbs", "alg_bytes_per_launch": dom_bytes},
+        "step_roofline": {"alg_bytes_per_step": ab["total"], "achieved_gbs": ab["total"] / (ms_step * 1e-3) / 1e9,
+                          "frac": ab["total"] / (ms_step * 1e-3) / 1e9 / peak,
+                          "with_gathered_vectors_gbs": (ab["total"] + ab["gathered_per_nonzero"]) / (ms_step * 1e-3) / 1e9},
+        "kernels": per_kernel,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "sources": src_hash,
+    }
+
+    # ---- end to end: host buffers through the public call ----
+    if rank == 0 or world > 1:
+        e2e = run_e2e(ttv, problem, subs, vals, vecs, fmt, args, dev)
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, m, dt = cpu_oracle_sample(problem)
+        line["cpu_baseline"] = {"value": v, "unit": "GNNZ/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {m} of {nnz} nonzeros, one call, {dt:.1f} s"}
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(ttv, problem, subs, vals, vecs, fmt, args, dev):
+    """Same metric through ttv_multi with HOST inputs: pinned host -> device
+    copies of subs, vals and vectors, the call, and the result read back, all
+    inside the timed region."""
+    store = subs.t().contiguous() if args.layout == "soa" else subs.contiguous()
+    h_store = store.cpu().pin_memory()
+    del store
+    h_vals = vals.cpu().pin_memory()
+    h_vecs = [v.cpu().pin_memory() for v in vecs]
+    d_subs_store = torch.empty_like(h_store, device=dev)
+    d_vals = torch.empty_like(h_vals, device=dev)
+    d_vecs = [torch.empty_like(v, device=dev) for v in h_vecs]
+    h2d = (d_subs_store.numel() * 8 + d_vals.numel() * d_vals.element_size() +
+           sum(v.numel() * v.element_size() for v in h_vecs))
+    d2h = 0
+    times = []
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        d_subs_store.copy_(h_store, non_blocking=True)
+        d_vals.copy_(h_vals, non_blocking=True)
+        for a, b in zip(d_vecs, h_vecs):
+            a.copy_(b, non_blocking=True)
+        ds = d_subs_store.t() if args.layout == "soa" else d_subs_store
+        r = ttv.ttv_multi(ds, d_vals, problem.tensor.shape, problem.modes, d_vecs, fmt=fmt, path=args.path)
+        hv = r.vals.cpu()
+        hs = r.subs.cpu() if r.subs is not None else None
+        torch.cuda.synchronize(dev)
+        if i > 0:
+            times.append(time.perf_counter() - t0)
+        d2h = hv.numel() * 8 + (hs.numel() * 8 if hs is not None else 0)
+    mean = sum(times) / len(times)
+    return {"value": problem.tensor.nnz / mean / 1e9, "unit": "GNNZ/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": mean * 1e3, "steps": len(times)}
+
+
+if __name__ == "__main__":
+    main()

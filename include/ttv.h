@@ -128,7 +128,8 @@ typedef struct {
     size_t workspace_bytes;
 } ttv_opts;
 
-/* Defaults: SPARSE, AUTO path, FP64, deterministic, synchronous, own workspace. */
+/* Defaults: SPARSE, AUTO path, FP64, not forced deterministic, synchronous,
+ * library-allocated workspace. */
 void ttv_opts_init(ttv_opts *opts);
 
 /* Single-vector TTV, A x_mode v (paper Eq. 3).  v is a device vector of
@@ -142,6 +143,13 @@ int ttv_single(const ttv_tensor *t, int32_t mode, const void *v, ttv_dtype v_dty
 int ttv_multi(const ttv_tensor *t, const int32_t *modes, int32_t n_v,
               const void *const *vecs, ttv_dtype v_dtype,
               ttv_out *out, const ttv_opts *opts, ttv_stream_t stream);
+
+/* ttv_multi with the vector lengths (host array, n_v entries) checked
+ * against shape[modes[i]] first (paper Sec. 3.3: each vector's size must be
+ * that of its mode); a mismatch returns TTV_ERR_VEC_LEN. */
+int ttv_multi_checked(const ttv_tensor *t, const int32_t *modes, int32_t n_v,
+                      const void *const *vecs, const int64_t *vec_lens, ttv_dtype v_dtype,
+                      ttv_out *out, const ttv_opts *opts, ttv_stream_t stream);
 
 /* Upper bounds for caller-allocated results: rows of subs and number of
  * values.  Sparse: min(nnz, prod shape[R]) (at least 1 for order 0).
@@ -163,6 +171,27 @@ void ttv_out_free(ttv_out *out);
 
 /* Message for the calling thread's last error ("" if none). */
 const char *ttv_last_error(void);
+
+/* ---- measurement --------------------------------------------------------
+ * Every kernel launch of the library is counted; with profiling enabled a
+ * CUDA event pair brackets each launch on the launching stream.  The paper
+ * times whole calls with monotonic clocks over 30 trials after a warm-up call
+ * (Sec. 3 and Sec. 4); these hooks add the per-kernel device view. */
+
+/* Kernel launches the library has issued since load. */
+long long ttv_launch_count(void);
+/* on != 0: record an event pair around every subsequent launch. */
+void ttv_profile_enable(int on);
+/* Waits for the recorded events and adds their times to per-kernel totals. */
+int ttv_profile_collect(void);
+/* Total milliseconds and launches of one kernel (by its name, e.g.
+ * "dense_accum"); TTV_ERR_ARG if it has not run. */
+int ttv_profile_get(const char *kernel, double *total_ms, long long *launches);
+/* Newline-separated kernel names into buf (len bytes); with buf == NULL
+ * returns the length needed. */
+int ttv_profile_names(char *buf, size_t len);
+/* Clears the per-kernel totals. */
+void ttv_profile_reset(void);
 
 #ifdef __cplusplus
 }

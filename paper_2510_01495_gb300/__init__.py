@@ -1,0 +1,312 @@
+"""Sparse tensor-times-vector product (TTV) on GB300: Python binding.
+
+Thin ctypes marshalling over the C ABI in ``include/ttv.h`` (library
+``_lib/libttv_gb300.so``, built for sm_103a by ``_build.build()``).  Every
+step of the computation runs in the library's CUDA kernels; PyTorch only
+provides device memory and the stream.  There is no CPU fallback: without the
+compiled library or a CUDA device every call raises.
+
+The operation (paper Sec. 3.3, Eq. 3): for a sparse COO tensor with int64
+``subs`` (nnz x d) and ``vals`` and dense vectors ``vecs[i]`` on modes
+``modes[i]``,
+
+    B(i_R) = sum_{k : subs[k, R] = i_R} vals[k] * prod_i vecs[i][subs[k, modes[i]]]
+
+over the surviving modes R (increasing).  Sparse results are canonical COO
+(ascending lexicographic rows, one per distinct surviving tuple present in the
+input); dense results are row-major arrays of shape[R].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import _build
+
+TTV_MAX_D = 8
+_LIB_PATH = _build.LIB
+_lock = threading.Lock()
+_lib = None
+
+ERR = {
+    0: "TTV_OK", -1: "TTV_ERR_ARG", -2: "TTV_ERR_MODE", -3: "TTV_ERR_VEC_LEN", -4: "TTV_ERR_SUBSCRIPT",
+    -5: "TTV_ERR_KEY_OVERFLOW", -6: "TTV_ERR_BUDGET", -7: "TTV_ERR_TIMEOUT", -8: "TTV_ERR_CUDA",
+    -9: "TTV_ERR_CAPACITY", -10: "TTV_ERR_NOMEM", -11: "TTV_ERR_UNSUPPORTED",
+}
+FMT = {"sparse": 0, "dense": 1, "auto": 2}
+PATH = {"auto": 0, "dense": 1, "sort": 2, "hash": 3, "bucket": 4}
+ACCUM = {"fp64": 0, "compensated": 1}
+DTYPE = {torch.float64: 0, torch.float32: 1}
+
+
+class TTVError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERR.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERR.get(code, str(code))
+
+
+class Tensor(ctypes.Structure):
+    _fields_ = [("subs", ctypes.c_void_p), ("stride_nz", ctypes.c_int64), ("stride_mode", ctypes.c_int64),
+                ("vals", ctypes.c_void_p), ("val_dtype", ctypes.c_int), ("nnz", ctypes.c_int64),
+                ("shape", ctypes.POINTER(ctypes.c_int64)), ("d", ctypes.c_int32)]
+
+
+class Out(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("shape", ctypes.c_int64 * TTV_MAX_D), ("nnz", ctypes.c_int64),
+                ("subs", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("subs_capacity", ctypes.c_int64),
+                ("vals_capacity", ctypes.c_int64), ("dtype", ctypes.c_int), ("is_dense", ctypes.c_int32),
+                ("internal", ctypes.c_void_p)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("fmt", ctypes.c_int32), ("path", ctypes.c_int32), ("accum", ctypes.c_int32),
+                ("deterministic", ctypes.c_int32), ("async_", ctypes.c_int32), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+def _declare(lib):
+    P = ctypes.POINTER
+    lib.ttv_opts_init.argtypes = [P(Opts)]
+    lib.ttv_opts_init.restype = None
+    lib.ttv_last_error.restype = ctypes.c_char_p
+    lib.ttv_last_error.argtypes = []
+    lib.ttv_single.argtypes = [P(Tensor), ctypes.c_int32, ctypes.c_void_p, ctypes.c_int, P(Out), P(Opts), ctypes.c_void_p]
+    lib.ttv_single.restype = ctypes.c_int
+    lib.ttv_multi.argtypes = [P(Tensor), P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_void_p), ctypes.c_int,
+                              P(Out), P(Opts), ctypes.c_void_p]
+    lib.ttv_multi.restype = ctypes.c_int
+    lib.ttv_multi_checked.argtypes = [P(Tensor), P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_void_p),
+                                      P(ctypes.c_int64), ctypes.c_int, P(Out), P(Opts), ctypes.c_void_p]
+    lib.ttv_multi_checked.restype = ctypes.c_int
+    lib.ttv_out_capacity.argtypes = [P(Tensor), P(ctypes.c_int32), ctypes.c_int32, P(Opts), P(ctypes.c_int64),
+                                     P(ctypes.c_int64)]
+    lib.ttv_out_capacity.restype = ctypes.c_int
+    lib.ttv_workspace_size.argtypes = [P(Tensor), P(ctypes.c_int32), ctypes.c_int32, ctypes.c_int, P(Opts),
+                                       P(ctypes.c_size_t)]
+    lib.ttv_workspace_size.restype = ctypes.c_int
+    lib.ttv_out_sync.argtypes = [P(Out)]
+    lib.ttv_out_sync.restype = ctypes.c_int
+    lib.ttv_out_free.argtypes = [P(Out)]
+    lib.ttv_out_free.restype = None
+    return lib
+
+
+def build(verbose: bool = False) -> str:
+    """Compile the CUDA library for sm_103a (nvcc) and return its path."""
+    return _build.build(verbose=verbose)
+
+
+def load(path: str | None = None):
+    """Load the compiled library (building it first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or _LIB_PATH
+            if not os.path.exists(p):
+                p = build()
+            _lib = _declare(ctypes.CDLL(p))
+    return _lib
+
+
+def _check(lib, rc: int):
+    if rc != 0:
+        raise TTVError(rc, lib.ttv_last_error().decode(errors="replace"))
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_tensor(subs: torch.Tensor, vals: torch.Tensor, shape):
+    """C descriptor for a (nnz, d) subscript view of any strides (AoS when
+    row-major, SoA when it is the transpose of a (d, nnz) contiguous array)."""
+    if not subs.is_cuda or not vals.is_cuda:
+        raise ValueError("subs and vals must be CUDA tensors")
+    if subs.dtype != torch.int64:
+        raise TypeError("subs must be int64")
+    if vals.dtype not in DTYPE:
+        raise TypeError("vals must be float64 or float32")
+    d = len(shape)
+    if subs.dim() != 2 or subs.shape[1] != d or subs.shape[0] != vals.shape[0]:
+        raise ValueError("subs must be (nnz, d) and match vals")
+    if vals.dim() != 1 or (vals.numel() > 1 and vals.stride(0) != 1):
+        raise ValueError("vals must be a contiguous vector")
+    shp = (ctypes.c_int64 * max(1, d))(*[int(s) for s in shape])
+    t = Tensor(subs.data_ptr(), subs.stride(0), subs.stride(1), vals.data_ptr(), DTYPE[vals.dtype],
+               vals.shape[0], ctypes.cast(shp, ctypes.POINTER(ctypes.c_int64)), d)
+    t._keep = (shp, subs, vals)
+    return t
+
+
+def make_opts(fmt="sparse", path="auto", accum="fp64", deterministic=False, async_=False,
+              workspace: torch.Tensor | None = None):
+    o = Opts()
+    load().ttv_opts_init(ctypes.byref(o))
+    o.fmt = FMT[fmt]
+    o.path = PATH[path]
+    o.accum = ACCUM[accum]
+    o.deterministic = int(bool(deterministic))
+    o.async_ = int(bool(async_))
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    return o
+
+
+def workspace_size(subs, vals, shape, modes, vec_dtype=torch.float64, **opt) -> int:
+    lib = load()
+    t = make_tensor(subs, vals, shape)
+    m = (ctypes.c_int32 * len(modes))(*modes)
+    o = make_opts(**opt)
+    n = ctypes.c_size_t()
+    _check(lib, lib.ttv_workspace_size(ctypes.byref(t), m, len(modes), DTYPE[vec_dtype], ctypes.byref(o), ctypes.byref(n)))
+    return int(n.value)
+
+
+def out_capacity(subs, vals, shape, modes, **opt):
+    lib = load()
+    t = make_tensor(subs, vals, shape)
+    m = (ctypes.c_int32 * len(modes))(*modes)
+    o = make_opts(**opt)
+    r, v = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib, lib.ttv_out_capacity(ctypes.byref(t), m, len(modes), ctypes.byref(o), ctypes.byref(r), ctypes.byref(v)))
+    return int(r.value), int(v.value)
+
+
+class Result:
+    """Result of a TTV call: ``subs`` (nnz, order) int64 (None when dense),
+    ``vals`` (nnz,) or a dense array of ``shape``, all on the device."""
+
+    def __init__(self, subs, vals, shape, is_dense):
+        self.subs, self.vals, self.shape, self.is_dense = subs, vals, tuple(shape), is_dense
+
+    def __iter__(self):
+        return iter((self.subs, self.vals, self.shape))
+
+
+def ttv_multi(subs: torch.Tensor, vals: torch.Tensor, shape, modes, vecs, *, fmt="sparse", path="auto",
+              accum="fp64", deterministic=False, out_subs: torch.Tensor | None = None,
+              out_vals: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None) -> Result:
+    """TTV of a COO tensor with one vector per mode in ``modes`` (any order).
+
+    ``out_subs`` / ``out_vals`` / ``workspace`` may be preallocated (see
+    ``out_capacity`` and ``workspace_size``); otherwise they are allocated here
+    with torch.  Synchronises the stream once to learn the result size."""
+    lib = load()
+    modes = [int(m) for m in modes]
+    if len(vecs) != len(modes):
+        raise ValueError("one vector per mode")
+    vdt = vecs[0].dtype if vecs else torch.float64
+    for v in vecs:
+        if not v.is_cuda or v.dtype != vdt or v.dim() != 1 or (v.numel() > 1 and v.stride(0) != 1):
+            raise ValueError("vectors must be contiguous CUDA vectors of one dtype")
+    if vdt not in DTYPE:
+        raise TypeError("vectors must be float64 or float32")
+    t = make_tensor(subs, vals, shape)
+    m = (ctypes.c_int32 * len(modes))(*modes)
+    vp = (ctypes.c_void_p * len(vecs))(*[v.data_ptr() for v in vecs])
+    lens = (ctypes.c_int64 * len(vecs))(*[v.numel() for v in vecs])
+    d = len(shape)
+    rows, nvals = ctypes.c_int64(), ctypes.c_int64()
+    if workspace is None:
+        o0 = make_opts(fmt=fmt, path=path, accum=accum, deterministic=deterministic)
+        _check(lib, lib.ttv_out_capacity(ctypes.byref(t), m, len(modes), ctypes.byref(o0), ctypes.byref(rows), ctypes.byref(nvals)))
+        nbytes = ctypes.c_size_t()
+        _check(lib, lib.ttv_workspace_size(ctypes.byref(t), m, len(modes), DTYPE[vdt], ctypes.byref(o0), ctypes.byref(nbytes)))
+        workspace = torch.empty(max(1, nbytes.value), dtype=torch.uint8, device=subs.device)
+    else:
+        o0 = make_opts(fmt=fmt, path=path, accum=accum, deterministic=deterministic)
+        _check(lib, lib.ttv_out_capacity(ctypes.byref(t), m, len(modes), ctypes.byref(o0), ctypes.byref(rows), ctypes.byref(nvals)))
+    order = d - len(modes)
+    if out_vals is None:
+        out_vals = torch.empty(max(1, nvals.value), dtype=torch.float64, device=subs.device)
+    if out_subs is None and fmt != "dense" and order > 0:
+        out_subs = torch.empty((max(1, rows.value), order), dtype=torch.int64, device=subs.device)
+    o = make_opts(fmt=fmt, path=path, accum=accum, deterministic=deterministic, workspace=workspace)
+    res = Out()
+    res.vals = out_vals.data_ptr()
+    res.vals_capacity = out_vals.numel()
+    if out_subs is not None:
+        res.subs = out_subs.data_ptr()
+        res.subs_capacity = out_subs.shape[0]
+    else:
+        res.subs = None
+        res.subs_capacity = 0
+    try:
+        rc = lib.ttv_multi_checked(ctypes.byref(t), m, len(modes), vp, lens, DTYPE[vdt], ctypes.byref(res),
+                                   ctypes.byref(o), _stream_handle(stream))
+        _check(lib, rc)
+        newshape = tuple(int(res.shape[j]) for j in range(res.order))
+        n = int(res.nnz)
+        if res.is_dense:
+            return Result(None, out_vals[:n].view(newshape), newshape, True)
+        vals_out = out_vals[:n]
+        subs_out = out_subs[:n] if out_subs is not None else torch.zeros((n, 0), dtype=torch.int64, device=subs.device)
+        return Result(subs_out, vals_out, newshape, False)
+    finally:
+        lib.ttv_out_free(ctypes.byref(res))
+
+
+def ttv_single(subs, vals, shape, mode: int, v: torch.Tensor, **kw) -> Result:
+    """TTV with one vector along ``mode`` (paper Eq. 3)."""
+    return ttv_multi(subs, vals, shape, [mode], [v], **kw)
+
+
+# ---- measurement hooks (per-kernel CUDA-event timing, launch counts) --------
+
+def _declare_prof(lib):
+    if getattr(lib, "_prof_declared", False):
+        return lib
+    lib.ttv_launch_count.restype = ctypes.c_longlong
+    lib.ttv_launch_count.argtypes = []
+    lib.ttv_profile_enable.argtypes = [ctypes.c_int]
+    lib.ttv_profile_enable.restype = None
+    lib.ttv_profile_collect.restype = ctypes.c_int
+    lib.ttv_profile_collect.argtypes = []
+    lib.ttv_profile_get.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+    lib.ttv_profile_get.restype = ctypes.c_int
+    lib.ttv_profile_names.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    lib.ttv_profile_names.restype = ctypes.c_int
+    lib.ttv_profile_reset.argtypes = []
+    lib.ttv_profile_reset.restype = None
+    lib._prof_declared = True
+    return lib
+
+
+def launch_count() -> int:
+    """Kernel launches the library has issued since it was loaded."""
+    return int(_declare_prof(load()).ttv_launch_count())
+
+
+def profile_enable(on: bool = True):
+    _declare_prof(load()).ttv_profile_enable(1 if on else 0)
+
+
+def profile_collect():
+    lib = _declare_prof(load())
+    _check(lib, lib.ttv_profile_collect())
+
+
+def profile_reset():
+    _declare_prof(load()).ttv_profile_reset()
+
+
+def profile_get(kernel: str):
+    """(total milliseconds, launches) of one kernel since the last reset."""
+    lib = _declare_prof(load())
+    ms, n = ctypes.c_double(), ctypes.c_longlong()
+    lib.ttv_profile_get(kernel.encode(), ctypes.byref(ms), ctypes.byref(n))
+    return float(ms.value), int(n.value)
+
+
+def profile_names():
+    lib = _declare_prof(load())
+    need = lib.ttv_profile_names(None, 0)
+    buf = ctypes.create_string_buffer(max(1, need))
+    lib.ttv_profile_names(buf, len(buf))
+    return [x for x in buf.value.decode().split("\n") if x]

@@ -1,0 +1,457 @@
+// ttv_sort.cu -- stable LSD radix sort of (uint64 key, double term) pairs and
+// the segmented reduction that turns sorted pairs into the canonical COO result.
+//
+// The sort is a "onesweep" LSD radix sort (A. Adinets and D. Merrill,
+// "Onesweep: A Faster Least Significant Digit Radix Sort for GPUs", 2022):
+// one upfront pass histograms every digit of every key; then each 8-bit digit
+// pass ranks a tile of keys in shared memory (warp-level multi-split with
+// __match_any_sync), publishes the tile's per-digit counts with a decoupled
+// look-back across tiles, and scatters through a shared-memory staging buffer
+// so that global writes of one digit are contiguous.  Tiles take a ticket from
+// a global counter, so a tile only waits on tiles that are already running;
+// every wait is bounded and reports kErrTimeout instead of hanging.
+//
+// Stability matters: equal keys keep their input order, so the segmented
+// reduction that follows sums every group in input order and the result is
+// bit-identical from run to run.
+#include <cstdio>
+
+#include "ttv_internal.cuh"
+
+namespace ttv {
+
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;      // 4096 keys per tile
+constexpr int kHistStride = kRadix + 1;                    // +1: padding bucket for absent items
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kCountMask = (1u << 30) - 1;
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Exclusive scan of one value per thread over a 256-thread block.
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_t* warp_tot, uint32_t& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+        uint32_t t = warp_tot[w];
+        if (w < warp) before += t;
+        all += t;
+    }
+    total = all;
+    __syncthreads();
+    return before + inc - x;
+}
+
+// ---------------------------------------------------------------------------
+// Histogram of every digit pass in one read of the keys.
+__global__ void __launch_bounds__(256) k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int npass,
+                                                    uint32_t* __restrict__ hist) {
+    __shared__ uint32_t sh[8 * kRadix];
+    for (int i = threadIdx.x; i < npass * kRadix; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t k = __ldcs(keys + i);
+        for (int p = 0; p < npass; ++p) atomicAdd(&sh[p * kRadix + ((k >> (p * kRadixBits)) & (kRadix - 1))], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * kRadix; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// In place: hist[p][d] -> exclusive prefix over digits of pass p.
+__global__ void __launch_bounds__(256) k_radix_hist_scan(uint32_t* hist, int npass) {
+    __shared__ uint32_t wt[kSortWarps];
+    for (int p = 0; p < npass; ++p) {
+        uint32_t x = hist[p * kRadix + threadIdx.x];
+        uint32_t total;
+        uint32_t ex = block_exclusive_scan_256(x, wt, total);
+        hist[p * kRadix + threadIdx.x] = ex;
+        __syncthreads();
+    }
+}
+
+// One digit pass.  Dynamic shared memory: warp histograms, digit starts,
+// global bases and a 4096-pair staging buffer.
+struct OnesweepSmem {
+    uint32_t whist[kSortWarps * kHistStride];
+    uint32_t tile_start[kRadix];
+    uint32_t gbase[kRadix];
+    uint32_t warp_tot[kSortWarps];
+    uint32_t tile;
+    uint32_t pad[3];
+    uint64_t keys[kSortTile];
+    double vals[kSortTile];
+};
+
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint64_t* __restrict__ keys_in,
+                                                           const double* __restrict__ vals_in,
+                                                           uint64_t* __restrict__ keys_out,
+                                                           double* __restrict__ vals_out, int64_t n, int shift,
+                                                           const uint32_t* __restrict__ digit_off,
+                                                           uint32_t* lookback, uint32_t* ticket, Status* st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    OnesweepSmem& sm = *reinterpret_cast<OnesweepSmem*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    if (tid == 0) sm.tile = atomicAdd(ticket, 1u);
+    for (int i = tid; i < kSortWarps * kHistStride; i += kSortThreads) sm.whist[i] = 0;
+    __syncthreads();
+    const uint32_t tile = sm.tile;
+    const int64_t base = (int64_t)tile * kSortTile;
+
+    uint64_t k[kSortItems];
+    double v[kSortItems];
+    uint32_t dig[kSortItems];
+    uint32_t rank[kSortItems];
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const int64_t idx = base + warp * (kSortItems * 32) + i * 32 + lane;
+        if (idx < n) {
+            k[i] = __ldcs(keys_in + idx);
+            v[i] = __ldcs(vals_in + idx);
+            dig[i] = (uint32_t)(k[i] >> shift) & (kRadix - 1);
+        } else {
+            k[i] = 0;
+            v[i] = 0.0;
+            dig[i] = kRadix;     // padding bucket, never published or written
+        }
+    }
+    // Warp-level multi-split: rank of each item among equal digits of its warp.
+    uint32_t* wh = sm.whist + warp * kHistStride;
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const uint32_t mask = __match_any_sync(0xffffffffu, dig[i]);
+        const int leader = __ffs(mask) - 1;
+        uint32_t b = 0;
+        if (lane == leader) {
+            b = wh[dig[i]];
+            wh[dig[i]] = b + __popc(mask);
+        }
+        b = __shfl_sync(0xffffffffu, b, leader);
+        rank[i] = b + __popc(mask & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // Thread t owns digit t: prefix over warps, tile count, tile-local start.
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = sm.whist[w * kHistStride + tid];
+        sm.whist[w * kHistStride + tid] = cnt;
+        cnt += c;
+    }
+    uint32_t tile_total;
+    sm.tile_start[tid] = block_exclusive_scan_256(cnt, sm.warp_tot, tile_total);
+
+    // Decoupled look-back across tiles for digit t.
+    uint32_t* my = lookback + (size_t)tile * kRadix + tid;
+    uint32_t exclusive = 0;
+    if (tile == 0) {
+        st_relaxed(my, kFlagInc | cnt);
+    } else {
+        st_relaxed(my, kFlagAgg | cnt);
+        int64_t j = (int64_t)tile - 1;
+        while (j >= 0) {
+            const uint32_t* q = lookback + (size_t)j * kRadix + tid;
+            uint32_t val = 0;
+            bool ok = false;
+            for (uint32_t it = 0; it < (1u << 24); ++it) {
+                val = ld_relaxed(q);
+                if (val & (kFlagAgg | kFlagInc)) { ok = true; break; }
+                if (it > 32) __nanosleep(32);
+            }
+            if (!ok) { set_error(st, kErrTimeout); break; }
+            exclusive += val & kCountMask;
+            if (val & kFlagInc) break;
+            --j;
+        }
+        st_relaxed(my, kFlagInc | ((exclusive + cnt) & kCountMask));
+    }
+    sm.gbase[tid] = digit_off[tid] + exclusive;
+    __syncthreads();
+
+    // Scatter into shared memory in digit order (stable), then out.
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        if (dig[i] < (uint32_t)kRadix) {
+            const uint32_t pos = sm.tile_start[dig[i]] + sm.whist[warp * kHistStride + dig[i]] + rank[i];
+            sm.keys[pos] = k[i];
+            sm.vals[pos] = v[i];
+        }
+    }
+    __syncthreads();
+    const int tile_n = (int)min((int64_t)kSortTile, n - base);
+    for (int j = tid; j < tile_n; j += kSortThreads) {
+        const uint64_t kk = sm.keys[j];
+        const uint32_t d = (uint32_t)(kk >> shift) & (kRadix - 1);
+        const uint32_t out = sm.gbase[d] + (uint32_t)j - sm.tile_start[d];
+        keys_out[out] = kk;
+        vals_out[out] = sm.vals[j];
+    }
+}
+
+size_t sort_workspace_bytes(int64_t n, int bits) {
+    const int npass = bits <= 0 ? 0 : (bits + kRadixBits - 1) / kRadixBits;
+    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    size_t b = 0;
+    b += 2 * (size_t)n * sizeof(uint64_t) + 2 * (size_t)n * sizeof(double) + 4 * 256;
+    b += (size_t)npass * kRadix * sizeof(uint32_t) + 256;
+    b += (size_t)npass * ntiles * kRadix * sizeof(uint32_t) + 256;
+    b += 64 * sizeof(uint32_t) + 256;
+    return b;
+}
+
+int radix_sort_pairs(SortBuffers& sb, int64_t n, int bits, Status* st, cudaStream_t stream) {
+    const int npass = bits <= 0 ? 0 : (bits + kRadixBits - 1) / kRadixBits;
+    if (npass == 0 || n <= 1) return 0;
+    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    cudaMemsetAsync(sb.hist, 0, (size_t)npass * kRadix * sizeof(uint32_t), stream);
+    cudaMemsetAsync(sb.lookback, 0, (size_t)npass * ntiles * kRadix * sizeof(uint32_t), stream);
+    cudaMemsetAsync(sb.tickets, 0, 64 * sizeof(uint32_t), stream);
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int hblocks = (int)std::min<int64_t>((int64_t)nsm * 4, (n + 255) / 256);
+    TTV_LAUNCH("radix_hist", stream, k_radix_hist<<<hblocks, 256, 0, stream>>>(sb.keys[0], n, npass, sb.hist));
+    TTV_LAUNCH("radix_hist_scan", stream, k_radix_hist_scan<<<1, 256, 0, stream>>>(sb.hist, npass));
+    const size_t smem = sizeof(OnesweepSmem);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    int cur = 0;
+    for (int p = 0; p < npass; ++p) {
+        TTV_LAUNCH("onesweep", stream, k_onesweep<<<(unsigned)ntiles, kSortThreads, smem, stream>>>(
+            sb.keys[cur], sb.vals[cur], sb.keys[cur ^ 1], sb.vals[cur ^ 1], n, p * kRadixBits,
+            sb.hist + p * kRadix, sb.lookback + (size_t)p * ntiles * kRadix, sb.tickets + p, st));
+        cur ^= 1;
+    }
+    return cur;
+}
+
+// ---------------------------------------------------------------------------
+// Segmented reduction of sorted pairs.
+//
+// k_seg_heads marks the first pair of every run of equal keys, numbers the
+// runs with a chained scan across tiles and records where each run starts.
+// k_seg_sum sums runs of up to kShortSeg pairs in one thread (in sorted, i.e.
+// input, order) and queues longer runs for k_long_seg, where one warp sums a
+// run with a fixed lane assignment and a fixed shuffle tree.  Both write the
+// result row: the key delinearised into the surviving subscripts, and the sum.
+constexpr int kSegThreads = 256;
+constexpr int kSegItems = 16;
+constexpr int kSegTile = kSegThreads * kSegItems;
+constexpr int kShortSeg = 32;
+constexpr unsigned long long kFlag64Agg = 1ull << 62;
+constexpr unsigned long long kFlag64Inc = 2ull << 62;
+constexpr unsigned long long kCount64Mask = (1ull << 62) - 1;
+
+__global__ void __launch_bounds__(kSegThreads) k_seg_heads(const uint64_t* __restrict__ keys, int64_t n,
+                                                           uint32_t* __restrict__ seg_start,
+                                                           unsigned long long* lookback, uint32_t* ticket,
+                                                           Status* st) {
+    __shared__ uint32_t wt[kSortWarps];
+    __shared__ uint32_t s_tile;
+    __shared__ unsigned long long s_excl;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t base = (int64_t)tile * kSegTile + (int64_t)tid * kSegItems;
+    uint32_t headbits = 0, cnt = 0;
+    uint64_t prev = 0;
+    if (base > 0 && base <= n - 1) prev = keys[base - 1];
+#pragma unroll
+    for (int i = 0; i < kSegItems; ++i) {
+        const int64_t idx = base + i;
+        if (idx < n) {
+            const uint64_t k = keys[idx];
+            if (idx == 0 || k != prev) { headbits |= 1u << i; ++cnt; }
+            prev = k;
+        }
+    }
+    uint32_t tile_total;
+    const uint32_t ex = block_exclusive_scan_256(cnt, wt, tile_total);
+    if (tid == 0) {
+        unsigned long long* my = lookback + tile;
+        unsigned long long excl = 0;
+        if (tile == 0) {
+            st_relaxed64(my, kFlag64Inc | tile_total);
+        } else {
+            st_relaxed64(my, kFlag64Agg | tile_total);
+            int64_t j = (int64_t)tile - 1;
+            while (j >= 0) {
+                unsigned long long val = 0;
+                bool ok = false;
+                for (uint32_t it = 0; it < (1u << 24); ++it) {
+                    val = ld_relaxed64(lookback + j);
+                    if (val & (kFlag64Agg | kFlag64Inc)) { ok = true; break; }
+                    if (it > 32) __nanosleep(32);
+                }
+                if (!ok) { set_error(st, kErrTimeout); break; }
+                excl += val & kCount64Mask;
+                if (val & kFlag64Inc) break;
+                --j;
+            }
+            st_relaxed64(my, kFlag64Inc | (excl + tile_total));
+        }
+        s_excl = excl;
+        const int64_t ntiles = (n + kSegTile - 1) / kSegTile;
+        if ((int64_t)tile == ntiles - 1) {
+            st->nnz_out = excl + tile_total;
+            seg_start[excl + tile_total] = (uint32_t)n;
+        }
+    }
+    __syncthreads();
+    uint32_t g = (uint32_t)s_excl + ex;
+#pragma unroll
+    for (int i = 0; i < kSegItems; ++i)
+        if (headbits & (1u << i)) seg_start[g++] = (uint32_t)(base + i);
+}
+
+struct SegOut {
+    int64_t* subs;          // rows of the sparse result (nullptr when dense)
+    double* vals;           // values; dense: indexed by key
+    int64_t cap_rows;       // capacity in rows (sparse)
+    int dense;
+    int compensated;
+};
+
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+    s = a + b;
+    const double bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+__global__ void __launch_bounds__(256) k_seg_sum(const uint64_t* __restrict__ keys, const double* __restrict__ vals,
+                                                 const uint32_t* __restrict__ seg_start, StreamDesc p, SegOut o,
+                                                 uint32_t* __restrict__ long_list, Status* st) {
+    const unsigned long long U = *(volatile unsigned long long*)&st->nnz_out;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((unsigned long long)j >= U) return;
+    if (!o.dense && (unsigned long long)o.cap_rows < U) {
+        if (j == 0) set_error(st, kErrCapacity);
+        return;
+    }
+    const uint32_t s0 = seg_start[j], s1 = seg_start[j + 1];
+    const uint64_t key = keys[s0];
+    if (!o.dense) delinearise(p, key, o.subs + j * p.nr);
+    if (s1 - s0 > (uint32_t)kShortSeg) {
+        const unsigned long long slot = atomicAdd(&st->long_count, 1ull);
+        long_list[slot] = (uint32_t)j;
+        return;
+    }
+    double sum = 0.0, comp = 0.0;
+    if (o.compensated) {
+        for (uint32_t i = s0; i < s1; ++i) {
+            double s, e;
+            two_sum(sum, vals[i], s, e);
+            sum = s;
+            comp += e;
+        }
+        sum += comp;
+    } else {
+        for (uint32_t i = s0; i < s1; ++i) sum += vals[i];
+    }
+    o.vals[o.dense ? (int64_t)key : j] = sum;
+}
+
+__global__ void __launch_bounds__(256) k_long_seg(const uint64_t* __restrict__ keys, const double* __restrict__ vals,
+                                                  const uint32_t* __restrict__ seg_start,
+                                                  const uint32_t* __restrict__ long_list, SegOut o, Status* st) {
+    const unsigned long long L = *(volatile unsigned long long*)&st->long_count;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = warp; (unsigned long long)w < L; w += nwarps) {
+        const uint32_t j = long_list[w];
+        const uint32_t s0 = seg_start[j], s1 = seg_start[j + 1];
+        double sum = 0.0, comp = 0.0;
+        for (uint32_t i = s0 + lane; i < s1; i += 32) {
+            if (o.compensated) {
+                double s, e;
+                two_sum(sum, vals[i], s, e);
+                sum = s;
+                comp += e;
+            } else {
+                sum += vals[i];
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double os = __shfl_xor_sync(0xffffffffu, sum, off);
+            const double oc = __shfl_xor_sync(0xffffffffu, comp, off);
+            if (o.compensated) {
+                // combine (sum, comp) pairs in a fixed order: lower lane first
+                const bool lower = (lane & off) == 0;
+                const double a = lower ? sum : os, b = lower ? os : sum;
+                double s, e;
+                two_sum(a, b, s, e);
+                comp = (lower ? comp + oc : oc + comp) + e;
+                sum = s;
+            } else {
+                const bool lower = (lane & off) == 0;
+                sum = lower ? sum + os : os + sum;
+            }
+        }
+        if (lane == 0) {
+            const double r = o.compensated ? sum + comp : sum;
+            o.vals[o.dense ? (int64_t)keys[s0] : (int64_t)j] = r;
+        }
+    }
+}
+
+void launch_seg_reduce(const uint64_t* keys, const double* vals, int64_t n, uint32_t* seg_start,
+                       unsigned long long* lookback, uint32_t* ticket, uint32_t* long_list, const StreamDesc& p,
+                       const SegOut& o, Status* st, cudaStream_t stream) {
+    if (n <= 0) return;
+    const int64_t ntiles = (n + kSegTile - 1) / kSegTile;
+    cudaMemsetAsync(lookback, 0, (size_t)ntiles * sizeof(unsigned long long), stream);
+    cudaMemsetAsync(ticket, 0, sizeof(uint32_t), stream);
+    TTV_LAUNCH("seg_heads", stream, k_seg_heads<<<(unsigned)ntiles, kSegThreads, 0, stream>>>(keys, n, seg_start, lookback, ticket, st));
+    TTV_LAUNCH("seg_sum", stream, k_seg_sum<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(keys, vals, seg_start, p, o, long_list, st));
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    TTV_LAUNCH("long_seg", stream, k_long_seg<<<(unsigned)(nsm * 4), 256, 0, stream>>>(keys, vals, seg_start, long_list, o, st));
+}
+
+}  // namespace ttv

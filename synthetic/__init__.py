@@ -114,6 +114,15 @@ def distinct_subs(seed: int, shape, nnz: int, dist: str = "uniform", zipf_s: flo
         raise ValueError("more distinct nonzeros than cells")
     if nnz == 0:
         return torch.zeros((0, d), dtype=torch.int64, device=device)
+    if nnz > total // 4 and total <= 50_000_000:
+        # dense-ish: a seeded random permutation of all cells, first nnz kept
+        order = torch.argsort(rand_bits(seed, 99, 0, total, device), stable=True)[:nnz]
+        cols = []
+        rem = order
+        for n in reversed(shape):
+            cols.append(rem % int(n))
+            rem = rem // int(n)
+        return torch.stack(cols[::-1], dim=1).contiguous()
     kept = None
     drawn = 0
     batch = max(16, int(nnz * 1.05) + 16)

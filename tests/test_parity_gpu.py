@@ -1,0 +1,145 @@
+"""CUDA path vs the CPU oracle, element by element, on seeded inputs that span
+several tiles with a ragged tail, plus the degenerate cases."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from parity import check_result, oracle_ttv, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+def run_case(ttv, problem, path="auto", fmt="sparse", layout="aos", val_dtype=torch.float64,
+             vec_dtype=torch.float64, accum="fp64", what=""):
+    subs, vals, vecs = to_device(problem, layout=layout, val_dtype=val_dtype, vec_dtype=vec_dtype)
+    dense = fmt == "dense"
+    ref, A = oracle_ttv(subs, vals, problem.tensor.shape, problem.modes, vecs, dense=dense)
+    res = ttv.ttv_multi(subs, vals, problem.tensor.shape, problem.modes, vecs, fmt=fmt, path=path, accum=accum)
+    check_result(res, ref, A, dense=dense, what=what or problem.name)
+    return res
+
+
+def rand_problem(seed, shape, nnz, modes, dist="uniform", vals="u11"):
+    t = S.sptenrand(seed, shape, nnz, dist=dist, vals=vals)
+    vecs = [S.vector(seed, m, shape[m]) for m in modes]
+    return S.Problem(t, list(modes), vecs, name=f"rand{seed}_{shape}_{nnz}_{modes}")
+
+
+@pytest.mark.parametrize("path", ["auto", "dense", "sort"])
+def test_single_3way_100(cuda_lib, path):
+    run_case(cuda_lib, S.single_3way_100(), path=path)
+
+
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+@pytest.mark.parametrize("path", ["dense", "sort"])
+@pytest.mark.parametrize("case", [
+    ((7, 9, 11), 600, [1]),
+    ((30, 20, 10, 5), 20_000, [0, 3]),
+    ((50, 40, 30), 9_001, [2]),
+    ((5, 6, 7, 8, 9), 7_777, [4, 0, 2]),
+    ((1000,), 999, [0]),
+    ((40, 50), 1_999, [1]),
+])
+def test_random_small(cuda_lib, case, path, layout):
+    shape, nnz, modes = case
+    p = rand_problem(11 + nnz, shape, nnz, modes)
+    run_case(cuda_lib, p, path=path, layout=layout)
+
+
+@pytest.mark.parametrize("path", ["dense", "sort"])
+def test_dense_format(cuda_lib, path):
+    p = rand_problem(5, (20, 30, 40), 5_000, [0])
+    run_case(cuda_lib, p, path=path, fmt="dense")
+
+
+def test_allbutone_4way_reduced(cuda_lib):
+    p = S.allbutone_4way_1000(nnz=300_000)
+    run_case(cuda_lib, p, fmt="dense")
+    run_case(cuda_lib, p, fmt="dense", path="sort")
+
+
+def test_zipf_5way_reduced(cuda_lib):
+    shape = (2000, 500, 10000, 200, 50)
+    p = S.single_5way_zipf(nnz=400_000, shape=shape)
+    res = run_case(cuda_lib, p, path="sort")
+    assert res.vals.numel() > 100_000
+
+
+@pytest.mark.parametrize("path", ["dense", "sort"])
+def test_float32_storage(cuda_lib, path):
+    p = rand_problem(21, (60, 70, 80), 30_000, [1])
+    run_case(cuda_lib, p, path=path, val_dtype=torch.float32, vec_dtype=torch.float32)
+
+
+@pytest.mark.parametrize("path", ["dense", "sort"])
+def test_compensated(cuda_lib, path):
+    p = rand_problem(22, (60, 70, 80), 30_000, [1])
+    run_case(cuda_lib, p, path=path, accum="compensated")
+
+
+def test_order0_scalar(cuda_lib):
+    p = rand_problem(23, (9, 8, 7), 300, [0, 1, 2])
+    res = run_case(cuda_lib, p)
+    assert res.vals.numel() == 1 and res.shape == ()
+
+
+def test_empty(cuda_lib):
+    dev = "cuda"
+    subs = torch.zeros((0, 3), dtype=torch.int64, device=dev)
+    vals = torch.zeros(0, dtype=torch.float64, device=dev)
+    v = torch.ones(4, dtype=torch.float64, device=dev)
+    r = cuda_lib.ttv_single(subs, vals, (3, 4, 5), 1, v)
+    assert r.shape == (3, 5) and r.vals.numel() == 0 and r.subs.shape == (0, 2)
+    r = cuda_lib.ttv_single(subs, vals, (3, 4, 5), 1, v, fmt="dense")
+    assert r.vals.shape == (3, 5) and float(r.vals.abs().sum()) == 0.0
+    r = cuda_lib.ttv_multi(subs, vals, (3, 4, 5), [0, 1, 2],
+                           [torch.ones(n, dtype=torch.float64, device=dev) for n in (3, 4, 5)])
+    assert r.shape == () and r.vals.numel() == 1 and float(r.vals[0]) == 0.0
+
+
+@pytest.mark.parametrize("path", ["dense", "sort"])
+def test_duplicates_and_heavy_segments(cuda_lib, path):
+    # one surviving tuple repeated 5000 times (long segment), duplicates of input subs
+    g = np.random.default_rng(3)
+    n = 12_000
+    subs = np.stack([g.integers(0, 3, n), g.integers(0, 50, n), g.integers(0, 2, n)], axis=1)
+    subs[:5000, 0] = 1
+    subs[:5000, 2] = 1
+    vals = g.uniform(-1, 1, n)
+    x = g.uniform(-1, 1, 50)
+    p = S.Problem(S.SparseTensor(torch.from_numpy(subs), torch.from_numpy(vals), (3, 50, 2)), [1],
+                  [torch.from_numpy(x)], name="heavy")
+    run_case(cuda_lib, p, path=path)
+
+
+def test_sort_is_deterministic(cuda_lib):
+    p = rand_problem(31, (300, 200, 100), 200_000, [1])
+    subs, vals, vecs = to_device(p)
+    r1 = cuda_lib.ttv_multi(subs, vals, p.tensor.shape, p.modes, vecs, path="sort")
+    r2 = cuda_lib.ttv_multi(subs, vals, p.tensor.shape, p.modes, vecs, path="sort")
+    assert torch.equal(r1.subs, r2.subs) and torch.equal(r1.vals, r2.vals)
+
+
+def test_errors(cuda_lib):
+    dev = "cuda"
+    subs = torch.tensor([[0, 1], [1, 2]], dtype=torch.int64, device=dev)
+    vals = torch.tensor([1.0, 2.0], dtype=torch.float64, device=dev)
+    with pytest.raises(cuda_lib.TTVError) as e:
+        cuda_lib.ttv_single(subs, vals, (2, 2), 0, torch.ones(2, dtype=torch.float64, device=dev))
+    assert e.value.name == "TTV_ERR_SUBSCRIPT"
+    subs = torch.tensor([[0, 1], [1, 0]], dtype=torch.int64, device=dev)
+    with pytest.raises(cuda_lib.TTVError) as e:
+        cuda_lib.ttv_single(subs, vals, (2, 2), 2, torch.ones(2, dtype=torch.float64, device=dev))
+    assert e.value.name == "TTV_ERR_MODE"
+    with pytest.raises(cuda_lib.TTVError) as e:
+        cuda_lib.ttv_multi(subs, vals, (2, 2), [0, 0], [torch.ones(2, dtype=torch.float64, device=dev)] * 2)
+    assert e.value.name == "TTV_ERR_MODE"
+    with pytest.raises(cuda_lib.TTVError) as e:
+        cuda_lib.ttv_single(subs, vals, (2, 2), 0, torch.ones(3, dtype=torch.float64, device=dev))
+    assert e.value.name == "TTV_ERR_VEC_LEN"
+    big = (1 << 32, 1 << 32, 2)
+    with pytest.raises(cuda_lib.TTVError) as e:
+        cuda_lib.ttv_single(torch.zeros((1, 3), dtype=torch.int64, device=dev), vals[:1], big, 2,
+                            torch.ones(2, dtype=torch.float64, device=dev))
+    assert e.value.name == "TTV_ERR_KEY_OVERFLOW"
