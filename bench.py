@@ -50,7 +50,8 @@ WORKLOADS = {
 # Kernel whose roofline is reported, per workload, and its algorithmic bytes
 # per launch: every nonzero's d subscripts and value read once, plus the
 # contracted vectors once.
-DOMINANT = {"allbutone_4way_1000": "dense_accum", "single_5way_zipf": "keys_terms", "single_3way_100": "dense_accum"}
+DOMINANT = {"allbutone_4way_1000": ["dense_accum", "dense_fx"], "single_5way_zipf": ["keys_terms"],
+            "single_3way_100": ["dense_accum", "dense_fx"]}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel from an ncu capture, with the sha1 of the kernel sources it was taken
@@ -203,6 +204,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="allbutone_4way_1000", choices=sorted(WORKLOADS))
     ap.add_argument("--path", default="auto")
+    ap.add_argument("--accum", default="fp64", choices=["fp64", "compensated", "exact"])
     ap.add_argument("--layout", default="soa", choices=["soa", "aos"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--nnz", type=int, default=None, help="smaller case of the workload (profiling)")
@@ -242,7 +244,8 @@ def main():
     del t
 
     # preallocated workspace and result (the steady-state way to call the ABI)
-    ws_bytes = ttv.workspace_size(subs, vals, problem.tensor.shape, problem.modes, fmt=fmt, path=args.path)
+    ws_bytes = ttv.workspace_size(subs, vals, problem.tensor.shape, problem.modes, fmt=fmt, path=args.path,
+                                  accum=args.accum)
     workspace = torch.empty(max(1, ws_bytes), dtype=torch.uint8, device=dev)
     rows, nv = ttv.out_capacity(subs, vals, problem.tensor.shape, problem.modes, fmt=fmt, path=args.path)
     order = problem.tensor.d - len(problem.modes)
@@ -254,7 +257,7 @@ def main():
     modes_c = (ctypes.c_int32 * len(problem.modes))(*problem.modes)
     vecp = (ctypes.c_void_p * len(vecs))(*[v.data_ptr() for v in vecs])
     lens = (ctypes.c_int64 * len(vecs))(*[v.numel() for v in vecs])
-    opts = ttv.make_opts(fmt=fmt, path=args.path, workspace=workspace, async_=True)
+    opts = ttv.make_opts(fmt=fmt, path=args.path, accum=args.accum, workspace=workspace, async_=True)
     sh = ctypes.c_void_p(stream.cuda_stream)
 
     def submit():
@@ -327,8 +330,8 @@ def main():
     for name in ttv.profile_names():
         tot, n = ttv.profile_get(name)
         per_kernel[name] = {"ms_total": tot, "launches": n, "ms_avg": tot / max(1, n)}
-    dom = DOMINANT[args.workload]
-    if dom not in per_kernel and per_kernel:
+    dom = next((k for k in DOMINANT[args.workload] if k in per_kernel), None)
+    if dom is None and per_kernel:
         dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_total"])
     ab = algorithmic_bytes(problem, nnz_out if fmt != "dense" else int(np.prod([problem.tensor.shape[m] for m in range(problem.tensor.d) if m not in problem.modes])))
     dom_bytes = ab["input"] + ab["vectors"]
@@ -346,6 +349,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "layout": args.layout, "path": args.path,
+                   "accum": args.accum,
                    "nnz": nnz, "nnz_out": nnz_out, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -80,6 +80,8 @@ typedef enum {
 typedef enum {
     TTV_ACCUM_FP64 = 0,          /* IEEE binary64 additions                           */
     TTV_ACCUM_COMPENSATED = 1,   /* binary64 with two-sum error compensation          */
+    TTV_ACCUM_EXACT = 2          /* 128-bit fixed point, order independent; the dense
+                                    path's deterministic mode                         */
 } ttv_accum;
 
 /* Input tensor.  subs[k * stride_nz + m * stride_mode] is subscript m of

@@ -38,7 +38,7 @@ ERR = {
 }
 FMT = {"sparse": 0, "dense": 1, "auto": 2}
 PATH = {"auto": 0, "dense": 1, "sort": 2, "hash": 3, "bucket": 4}
-ACCUM = {"fp64": 0, "compensated": 1}
+ACCUM = {"fp64": 0, "compensated": 1, "exact": 2}
 DTYPE = {torch.float64: 0, torch.float32: 1}
 
 

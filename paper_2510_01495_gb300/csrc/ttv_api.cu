@@ -86,6 +86,7 @@ struct OutState {
     void* owned_vals = nullptr;
     int dense_out = 0;
     int finalized = 0;
+    int nonfinite = 0;          // fixed-point path met inf/nan: rerun in binary64
     int rc = TTV_OK;
 };
 
@@ -102,8 +103,20 @@ struct Arena {
     }
 };
 
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    }
+    return n;
+}
+
 struct Plan {
     StreamDesc desc;
+    FxPlan fx{};
+    int use_fx = 0;             // dense path on the fixed-point kernel
     int path = TTV_PATH_DENSE;
     int dense_out = 0;          // result written as a dense array
     int order0 = 0;
@@ -123,7 +136,7 @@ static int bits_for(uint64_t nkeys) {
 }
 
 static int make_plan(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const void* const* vecs,
-                     ttv_dtype vd, const int64_t* vec_lens, const ttv_opts* o, Plan& pl) {
+                     ttv_dtype vd, const int64_t* vec_lens, const ttv_opts* o, Plan& pl, bool force_fp64 = false) {
     if (!t || !o) return fail(TTV_ERR_ARG, "null tensor or options");
     if (t->d < 1 || t->d > TTV_MAX_D) return fail(TTV_ERR_ARG, "order d=%d outside 1..%d", t->d, TTV_MAX_D);
     if (t->nnz < 0) return fail(TTV_ERR_ARG, "negative nnz");
@@ -135,6 +148,7 @@ static int make_plan(const ttv_tensor* t, const int32_t* modes, int32_t n_v, con
     if (!modes || !vecs) return fail(TTV_ERR_ARG, "null modes or vectors");
     if (o->fmt < TTV_OUT_SPARSE || o->fmt > TTV_OUT_AUTO) return fail(TTV_ERR_ARG, "bad output format");
     if (o->path < TTV_PATH_AUTO || o->path > TTV_PATH_BUCKET) return fail(TTV_ERR_ARG, "bad path");
+    if (o->accum < TTV_ACCUM_FP64 || o->accum > TTV_ACCUM_EXACT) return fail(TTV_ERR_ARG, "bad accumulation mode");
     for (int m = 0; m < t->d; ++m)
         if (t->shape[m] < 1) return fail(TTV_ERR_ARG, "shape[%d]=%lld < 1", m, (long long)t->shape[m]);
 
@@ -189,13 +203,18 @@ static int make_plan(const ttv_tensor* t, const int32_t* modes, int32_t n_v, con
 
     int path = o->path;
     const bool dense_ok = (int64_t)p.nkeys <= kDenseMaxCells;
-    if (path == TTV_PATH_AUTO) {
-        if (dense_ok && !(o->deterministic && !pl.order0 && p.nnz > 0)) path = TTV_PATH_DENSE;
-        else path = TTV_PATH_SORT;
-        if (pl.order0) path = TTV_PATH_DENSE;
-    }
+    const bool want_exact = o->accum == TTV_ACCUM_EXACT || o->deterministic;
+    if (path == TTV_PATH_AUTO) path = (dense_ok || pl.order0) ? TTV_PATH_DENSE : TTV_PATH_SORT;
     if (path == TTV_PATH_HASH || path == TTV_PATH_BUCKET) path = TTV_PATH_SORT;   // not built yet: sort
     if (path == TTV_PATH_DENSE && !dense_ok) return fail(TTV_ERR_UNSUPPORTED, "dense path needs prod shape[R] <= %lld", (long long)kDenseMaxCells);
+    if (path == TTV_PATH_DENSE) {
+        // exact fixed point when asked for determinism (binary64 shared-memory
+        // atomics are order dependent); binary64 atomics otherwise
+        const int presence = !pl.dense_out;
+        pl.fx = plan_dense_fx(p, presence, num_sms());
+        pl.use_fx = want_exact && pl.fx.ok && !force_fp64 && p.nnz > 0;
+        if (want_exact && !pl.fx.ok && !pl.order0 && p.nnz > 0) path = TTV_PATH_SORT;
+    }
     if (path == TTV_PATH_SORT && p.nnz > kMaxSortN) return fail(TTV_ERR_UNSUPPORTED, "sort path supports nnz < 2^30");
     pl.path = path;
     pl.want_presence = (path == TTV_PATH_DENSE) && !pl.dense_out;
@@ -208,7 +227,7 @@ static int make_plan(const ttv_tensor* t, const int32_t* modes, int32_t n_v, con
         pl.cap_rows = r;
         pl.cap_vals = r;
     }
-    if (path == TTV_PATH_DENSE) pl.grid = dense_grid(p, pl.want_presence);
+    if (path == TTV_PATH_DENSE && !pl.use_fx) pl.grid = dense_grid(p, pl.want_presence);
     return TTV_OK;
 }
 
@@ -216,6 +235,7 @@ static int make_plan(const ttv_tensor* t, const int32_t* modes, int32_t n_v, con
 struct WsPtrs {
     Status* status;
     // dense
+    void* fx_ws;
     double* partials;
     uint32_t* pres_partials;
     double* cell_vals;
@@ -234,9 +254,13 @@ static void layout(const Plan& pl, Arena& a, WsPtrs& w) {
     w.status = a.take<Status>(1);
     if (pl.path == TTV_PATH_DENSE) {
         const int64_t P = (int64_t)p.nkeys;
-        w.partials = a.take<double>((size_t)pl.grid * P);
+        if (pl.use_fx) {
+            w.fx_ws = a.take<char>(dense_fx_workspace(p, pl.fx, pl.want_presence));
+        } else {
+            w.partials = a.take<double>((size_t)pl.grid * P);
+            if (pl.want_presence) w.pres_partials = a.take<uint32_t>((size_t)pl.grid * ((P + 31) / 32));
+        }
         if (pl.want_presence) {
-            w.pres_partials = a.take<uint32_t>((size_t)pl.grid * ((P + 31) / 32));
             w.cell_vals = a.take<double>(P);
             w.cell_flags = a.take<uint32_t>(P);
         }
@@ -281,6 +305,10 @@ static int finalize(ttv_out* out) {
     if (h.err & kErrTimeout) return s->rc = fail(TTV_ERR_TIMEOUT, "a bounded device wait ran out");
     if (h.err & kErrCapacity) return s->rc = fail(TTV_ERR_CAPACITY, "result (%llu rows) exceeds the output buffer", (unsigned long long)h.nnz_out);
     if (h.err & kErrInternal) return s->rc = fail(TTV_ERR_CUDA, "internal device check failed");
+    if (h.err & kErrNonFinite) {
+        s->nonfinite = 1;
+        return s->rc = fail(TTV_ERR_UNSUPPORTED, "non-finite input on the fixed-point dense path");
+    }
     return s->rc = TTV_OK;
 }
 
@@ -346,8 +374,11 @@ static int execute(const Plan& pl, ttv_out* out, const ttv_opts* o, cudaStream_t
         if (pl.dense_out) cudaMemsetAsync(ovals, 0, (size_t)std::max<int64_t>(pl.cap_vals, 1) * sizeof(double), stream);
     } else if (pl.path == TTV_PATH_DENSE) {
         double* cell_vals = pl.want_presence ? w.cell_vals : ovals;
-        launch_dense(p, pl.want_presence, pl.compensated, pl.grid, w.partials, w.pres_partials, cell_vals,
-                     w.cell_flags, stream);
+        if (pl.use_fx)
+            launch_dense_fx(p, pl.fx, pl.want_presence, w.fx_ws, cell_vals, w.cell_flags, stream);
+        else
+            launch_dense(p, pl.want_presence, pl.compensated, pl.grid, w.partials, w.pres_partials, cell_vals,
+                         w.cell_flags, stream);
         if (pl.want_presence) launch_compact_cells(p, w.cell_vals, w.cell_flags, cap_rows_eff, out->subs, ovals, stream);
     } else {
         launch_keys_terms(p, w.sb.keys[0], w.sb.vals[0], stream);
@@ -415,7 +446,27 @@ int ttv_multi_checked(const ttv_tensor* t, const int32_t* modes, int32_t n_v, co
     Plan pl;
     int rc = make_plan(t, modes, n_v, vecs, v_dtype, vec_lens, o, pl);
     if (rc != TTV_OK) return rc;
-    return execute(pl, out, o, reinterpret_cast<cudaStream_t>(stream));
+    rc = execute(pl, out, o, reinterpret_cast<cudaStream_t>(stream));
+    OutState* s = static_cast<OutState*>(out->internal);
+    if (rc == TTV_ERR_UNSUPPORTED && s && s->nonfinite) {
+        // inf or nan in the input: the binary64 kernel propagates them like the definition
+        Plan p2;
+        rc = make_plan(t, modes, n_v, vecs, v_dtype, vec_lens, o, p2, /*force_fp64=*/true);
+        if (rc != TTV_OK) return rc;
+        void* keep_subs = s->owned_subs;
+        void* keep_vals = s->owned_vals;
+        s->owned_subs = s->owned_vals = nullptr;
+        g_status_pool.release(s->hstatus);
+        delete s;
+        out->internal = nullptr;
+        rc = execute(p2, out, o, reinterpret_cast<cudaStream_t>(stream));
+        OutState* s2 = static_cast<OutState*>(out->internal);
+        if (s2) {
+            s2->owned_subs = keep_subs;
+            s2->owned_vals = keep_vals;
+        }
+    }
+    return rc;
 }
 
 int ttv_multi(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const void* const* vecs, ttv_dtype v_dtype,

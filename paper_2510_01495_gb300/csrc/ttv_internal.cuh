@@ -18,6 +18,7 @@ enum : uint32_t {
     kErrTimeout = 1u << 1,     // a bounded spin wait ran out
     kErrCapacity = 1u << 2,    // result larger than the output buffer
     kErrInternal = 1u << 3,    // an internal invariant failed (bucket overflow ...)
+    kErrNonFinite = 1u << 4,   // inf/nan met by a fixed-point accumulator
 };
 
 // Per-call device status block (lives in the call's workspace).
@@ -56,6 +57,105 @@ struct StreamDesc {
 
 __device__ __forceinline__ void set_error(Status* st, uint32_t bit) {
     atomicOr(&st->err, bit);
+}
+
+
+// ---- exact significand arithmetic (integer units; GB300's FP64 pipe is ~2/clk/SM) ----
+// |x| = M * 2^(E - 63) with M in [2^63, 2^64); zero gives M = 0.
+struct Sig {
+    unsigned long long M;
+    int E;
+    uint32_t neg;
+    uint32_t bad;     // inf or nan
+};
+
+__device__ __forceinline__ Sig decompose(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    Sig s;
+    s.neg = (uint32_t)(b >> 63);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    const unsigned long long f = b & ((1ull << 52) - 1);
+    s.bad = ex == 0x7FF;
+    if (ex == 0) {
+        if (f == 0) {
+            s.M = 0;
+            s.E = -(1 << 28);
+        } else {
+            const int lz = __clzll(f);
+            s.M = f << lz;
+            s.E = -1011 - lz;
+        }
+    } else {
+        s.M = (f | (1ull << 52)) << 11;
+        s.E = ex - 1023;
+    }
+    return s;
+}
+
+// a *= b on significands: high 64 bits of the 128-bit product, renormalised
+// (truncation error below 2^-62 relative).
+__device__ __forceinline__ void sig_mul(Sig& a, const Sig& b) {
+    const unsigned long long hi = __umul64hi(a.M, b.M);
+    const bool top = (hi >> 63) != 0;
+    a.M = top ? hi : (hi << 1);
+    a.E = a.E + b.E + (top ? 1 : 0);
+    a.neg ^= b.neg;
+    a.bad |= b.bad;
+    if (b.M == 0) a.M = 0;
+}
+
+// Nearest binary64 of a significand (ties to even); infinities and
+// subnormal results take the general scalbn route.
+__device__ __forceinline__ double sig_to_double(const Sig& s) {
+    if (s.M == 0) return s.neg ? -0.0 : 0.0;
+    unsigned long long mant = s.M >> 11;                 // 53 bits, top bit set
+    const unsigned long long rest = s.M & 0x7FFull;
+    if (rest > 0x400ull || (rest == 0x400ull && (mant & 1ull))) ++mant;
+    int E = s.E;
+    if (mant >> 53) { mant >>= 1; ++E; }
+    if (E >= -1022 && E <= 1023) {
+        const unsigned long long bits = ((unsigned long long)s.neg << 63) |
+                                        ((unsigned long long)(E + 1023) << 52) | (mant & ((1ull << 52) - 1));
+        return __longlong_as_double((long long)bits);
+    }
+    const double r = scalbn((double)(s.M >> 11), E - 52);
+    return s.neg ? -r : r;
+}
+
+// A staged vector entry, decomposed once per CTA (16 bytes: one LDS.128).
+struct __align__(16) SigEntry {
+    unsigned long long M;
+    int E;
+    uint32_t neg_bad;    // bit 0: sign, bit 1: inf/nan
+};
+
+__device__ __forceinline__ Sig sig_of(const SigEntry& e) {
+    Sig s;
+    s.M = e.M;
+    s.E = e.E;
+    s.neg = e.neg_bad & 1u;
+    s.bad = (e.neg_bad >> 1) & 1u;
+    return s;
+}
+
+// Stage the contracted vectors in shared memory as decomposed significands.
+__device__ __forceinline__ void stage_vectors_sig(const StreamDesc& p, SigEntry* sv) {
+    if (!p.vec_smem) return;
+    for (int m = 0; m < p.d; ++m) {
+        if (!((p.smask >> m) & 1u)) continue;
+        const int64_t n = p.shape[m];
+        SigEntry* dst = sv + p.voff[m];
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const double x = p.vec_f32 ? (double)__ldg(static_cast<const float*>(p.vec[m]) + i)
+                                       : __ldg(static_cast<const double*>(p.vec[m]) + i);
+            const Sig s = decompose(x);
+            SigEntry e;
+            e.M = s.M;
+            e.E = s.E;
+            e.neg_bad = s.neg | (s.bad << 1);
+            dst[i] = e;
+        }
+    }
 }
 
 // Stage the contracted vectors in shared memory as doubles (exact for floats).
@@ -127,6 +227,47 @@ __device__ __forceinline__ bool key_term(const StreamDesc& p, const double* sv, 
     return good;
 }
 
+// Same as key_term with the product formed on integer units: the value and
+// each gathered entry as significands, multiplied exactly to 64 bits and
+// rounded once to binary64 (within one unit of the binary64 product chain).
+// Inf/nan operands take the binary64 chain so they propagate as usual.
+__device__ __forceinline__ bool key_term_sig(const StreamDesc& p, const SigEntry* sve, const int64_t* s, double val,
+                                             uint64_t& key, double& t) {
+    bool good = true;
+    uint64_t kk = 0;
+    Sig acc = decompose(val);
+#pragma unroll
+    for (int m = 0; m < kMaxD; ++m) {
+        if (m >= p.d) break;
+        const int64_t sm = s[m];
+        if (sm < 0 || sm >= p.shape[m]) { good = false; continue; }
+        if ((p.smask >> m) & 1u) {
+            if (p.vec_smem) {
+                sig_mul(acc, sig_of(sve[p.voff[m] + sm]));
+            } else {
+                const double x = p.vec_f32 ? (double)__ldg(static_cast<const float*>(p.vec[m]) + sm)
+                                           : __ldg(static_cast<const double*>(p.vec[m]) + sm);
+                sig_mul(acc, decompose(x));
+            }
+        } else {
+            kk += (uint64_t)sm * p.kstride[m];
+        }
+    }
+    key = kk;
+    if (good && acc.bad) {
+        double tt = val;
+#pragma unroll
+        for (int m = 0; m < kMaxD; ++m)
+            if (m < p.d && ((p.smask >> m) & 1u))
+                tt = tt * (p.vec_f32 ? (double)__ldg(static_cast<const float*>(p.vec[m]) + s[m])
+                                     : __ldg(static_cast<const double*>(p.vec[m]) + s[m]));
+        t = tt;
+    } else {
+        t = sig_to_double(acc);
+    }
+    return good;
+}
+
 // Inverse of the linearisation: key -> result subscripts (row-major over R).
 __device__ __forceinline__ void delinearise(const StreamDesc& p, uint64_t key, int64_t* out_row) {
     for (int j = p.nr - 1; j >= 0; --j) {
@@ -160,6 +301,19 @@ void prof_end(cudaStream_t s);
     } while (0)
 
 // ---- host-side launch helpers (implemented in the .cu files) -------------
+
+// Plan of the fixed-point dense path (ttv_dense_fx.cu).
+struct FxPlan {
+    bool ok;
+    int tile, stages, grid, headroom, aos;
+    size_t stage_bytes, smem_total, cells_off, pres_off, vec_off, stage_off, bar_off;
+    int64_t chunk;
+};
+FxPlan plan_dense_fx(const StreamDesc& p, int want_presence, int num_sms);
+size_t dense_fx_workspace(const StreamDesc& p, const FxPlan& fp, int want_presence);
+void launch_dense_fx(const StreamDesc& p, const FxPlan& fp, int want_presence, void* ws, double* cell_vals,
+                     uint32_t* cell_flags, cudaStream_t stream);
+int num_sms();
 
 struct SortBuffers {
     uint64_t* keys[2];

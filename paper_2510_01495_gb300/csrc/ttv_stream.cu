@@ -69,6 +69,12 @@ struct DenseSmemLayout {
     size_t acc_off, pres_off, vec_off, total;
 };
 
+// Products on integer units (exact significand multiplies) instead of the
+// binary64 chain.  Off until the order-specialised kernels land: in the
+// generic kernel the extra integer instructions cost more than the FP64
+// multiplies they replace.
+static int use_int_products(const StreamDesc& p) { (void)p; return 0; }
+
 static DenseSmemLayout dense_layout(const StreamDesc& p, int want_presence) {
     DenseSmemLayout L;
     L.acc_off = 0;
@@ -77,11 +83,12 @@ static DenseSmemLayout dense_layout(const StreamDesc& p, int want_presence) {
     if (want_presence) off += ((p.nkeys + 31) / 32) * sizeof(uint32_t);
     off = (off + 15) & ~size_t(15);
     L.vec_off = off;
-    if (p.vec_smem) off += (size_t)p.vtotal * sizeof(double);
+    if (p.vec_smem) off += (size_t)p.vtotal * (use_int_products(p) ? sizeof(SigEntry) : sizeof(double));
     L.total = off;
     return L;
 }
 
+template <bool kIntProducts>
 __global__ void __launch_bounds__(kStreamThreads) k_dense_accum(StreamDesc p, int64_t chunk, int want_presence,
                                                                 size_t pres_off, size_t vec_off,
                                                                 double* __restrict__ partials,
@@ -90,12 +97,14 @@ __global__ void __launch_bounds__(kStreamThreads) k_dense_accum(StreamDesc p, in
     double* acc = reinterpret_cast<double*>(dsm);
     uint32_t* pres = reinterpret_cast<uint32_t*>(dsm + pres_off);
     double* sv = reinterpret_cast<double*>(dsm + vec_off);
+    SigEntry* sve = reinterpret_cast<SigEntry*>(dsm + vec_off);
     const int64_t P = (int64_t)p.nkeys;
     const int64_t npres = (P + 31) / 32;
     for (int64_t i = threadIdx.x; i < P; i += blockDim.x) acc[i] = 0.0;
     if (want_presence)
         for (int64_t i = threadIdx.x; i < npres; i += blockDim.x) pres[i] = 0u;
-    stage_vectors(p, sv);
+    if (kIntProducts) stage_vectors_sig(p, sve);
+    else stage_vectors(p, sv);
     __syncthreads();
 
     const int64_t lo = (int64_t)blockIdx.x * chunk;
@@ -115,7 +124,10 @@ __global__ void __launch_bounds__(kStreamThreads) k_dense_accum(StreamDesc p, in
             if (!ok[u]) continue;
             uint64_t key;
             double t;
-            if (!key_term(p, sv, b.s[u], b.v[u], key, t)) {
+            bool good;
+            if constexpr (kIntProducts) good = key_term_sig(p, sve, b.s[u], b.v[u], key, t);
+            else good = key_term(p, sv, b.s[u], b.v[u], key, t);
+            if (!good) {
                 set_error(p.status, kErrSubscript);
                 continue;
             }
@@ -224,8 +236,13 @@ int dense_grid(const StreamDesc& p, int want_presence) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = dense_layout(p, want_presence).total;
     int per_sm = 1;
-    cudaFuncSetAttribute(k_dense_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_accum, kStreamThreads, smem);
+    if (use_int_products(p)) {
+        cudaFuncSetAttribute(k_dense_accum<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_accum<true>, kStreamThreads, smem);
+    } else {
+        cudaFuncSetAttribute(k_dense_accum<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_accum<false>, kStreamThreads, smem);
+    }
     per_sm = std::max(1, std::min(per_sm, 4));
     // at least ~4 unrolled sweeps of the block per CTA so that zeroing and
     // writing the partial array stay small next to the streaming work
@@ -238,9 +255,15 @@ void launch_dense(const StreamDesc& p, int want_presence, int compensated, int G
                   uint32_t* pres_partials, double* cell_vals, uint32_t* cell_flags, cudaStream_t stream) {
     const DenseSmemLayout L = dense_layout(p, want_presence);
     const int64_t chunk = std::max<int64_t>(1, (p.nnz + G - 1) / G);
-    cudaFuncSetAttribute(k_dense_accum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(L.total, 1));
-    TTV_LAUNCH("dense_accum", stream, k_dense_accum<<<G, kStreamThreads, L.total, stream>>>(p, chunk, want_presence, L.pres_off, L.vec_off, partials,
-                                                         pres_partials));
+    if (use_int_products(p)) {
+        cudaFuncSetAttribute(k_dense_accum<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(L.total, 1));
+        TTV_LAUNCH("dense_accum", stream, k_dense_accum<true><<<G, kStreamThreads, L.total, stream>>>(
+                                              p, chunk, want_presence, L.pres_off, L.vec_off, partials, pres_partials));
+    } else {
+        cudaFuncSetAttribute(k_dense_accum<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(L.total, 1));
+        TTV_LAUNCH("dense_accum", stream, k_dense_accum<false><<<G, kStreamThreads, L.total, stream>>>(
+                                              p, chunk, want_presence, L.pres_off, L.vec_off, partials, pres_partials));
+    }
     const int64_t P = (int64_t)p.nkeys;
     const int64_t blocks = (P * 32 + 255) / 256;
     TTV_LAUNCH("dense_reduce", stream, k_dense_reduce<<<(unsigned)blocks, 256, 0, stream>>>(P, G, partials, pres_partials, want_presence, compensated,

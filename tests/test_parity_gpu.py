@@ -143,3 +143,41 @@ def test_errors(cuda_lib):
         cuda_lib.ttv_single(torch.zeros((1, 3), dtype=torch.int64, device=dev), vals[:1], big, 2,
                             torch.ones(2, dtype=torch.float64, device=dev))
     assert e.value.name == "TTV_ERR_KEY_OVERFLOW"
+
+
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+@pytest.mark.parametrize("case", [
+    ((7, 9, 11), 600, [1], "sparse"),
+    ((30, 20, 10, 5), 20_000, [0, 3], "sparse"),
+    ((30, 20, 10, 5), 20_001, [0, 1, 3], "dense"),
+    ((5, 6, 7, 8, 9), 7_777, [4, 0, 2], "dense"),
+    ((9, 8, 7), 401, [0, 1, 2], "sparse"),
+])
+def test_exact_fixed_point(cuda_lib, case, layout):
+    shape, nnz, modes, fmt = case
+    p = rand_problem(101 + nnz, shape, nnz, modes)
+    run_case(cuda_lib, p, path="dense", fmt=fmt, layout=layout, accum="exact")
+
+
+def test_exact_is_deterministic_and_float32(cuda_lib):
+    p = S.allbutone_4way_1000(nnz=400_000)
+    subs, vals, vecs = to_device(p, layout="soa")
+    r1 = cuda_lib.ttv_multi(subs, vals, p.tensor.shape, p.modes, vecs, fmt="dense", accum="exact")
+    r2 = cuda_lib.ttv_multi(subs, vals, p.tensor.shape, p.modes, vecs, fmt="dense", accum="exact")
+    assert torch.equal(r1.vals, r2.vals)
+    run_case(cuda_lib, p, fmt="dense", accum="exact", layout="soa")
+    run_case(cuda_lib, p, fmt="dense", accum="exact", val_dtype=torch.float32, vec_dtype=torch.float32)
+
+
+def test_nonfinite_inputs_propagate(cuda_lib):
+    # inf / nan in the values: the exact path hands over to binary64 arithmetic
+    p = rand_problem(7, (20, 30, 40), 3_000, [0, 2])
+    subs, vals, vecs = to_device(p)
+    vals[5] = float("inf")
+    vals[9] = float("nan")
+    for accum in ("fp64", "exact"):
+        r = cuda_lib.ttv_multi(subs, vals, p.tensor.shape, p.modes, vecs, accum=accum)
+        ref, _ = oracle_ttv(subs, vals, p.tensor.shape, p.modes, vecs)
+        got = r.vals.cpu().numpy()
+        assert np.array_equal(np.isnan(got), np.isnan(ref[1]))
+        assert np.array_equal(np.isinf(got), np.isinf(ref[1]))
