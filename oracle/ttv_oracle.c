@@ -27,6 +27,8 @@
  *   - each group is summed in input order with Neumaier's compensated
  *     summation (A. Neumaier, ZAMM 54, 1974), so the oracle's own error is a
  *     few units in the last place of the exact group sum of the rounded terms;
+ *     when the running sum is not finite the plain IEEE sum is the result
+ *     (the correction term would turn a lone infinity into a NaN);
  *   - n_v == d gives an order-0 result: one scalar, the multilinear form.
  *
  * Build with -ffp-contract=off: a fused multiply-add would change the rounding
@@ -177,7 +179,7 @@ int oracle_ttv(int32_t d, const int64_t *shape, int64_t nnz,
     for (int64_t i = 0; i < nnz; ++i) {
         int64_t k = idx[i];
         if (i == 0 || !same_row(&ctx, idx[i - 1], k)) {
-            if (g >= 0) gvals[g] = sum + comp;
+            if (g >= 0) gvals[g] = isfinite(sum) ? sum + comp : sum;
             ++g;
             for (int32_t j = 0; j < ctx.nr; ++j) gsubs[g * ctx.nr + j] = subs[k * d + ctx.r[j]];
             sum = 0.0;
@@ -188,7 +190,7 @@ int oracle_ttv(int32_t d, const int64_t *shape, int64_t nnz,
         else                         comp += (t[k] - s) + sum;
         sum = s;
     }
-    if (g >= 0) gvals[g] = sum + comp;
+    if (g >= 0) gvals[g] = isfinite(sum) ? sum + comp : sum;
     free(t);
     free(idx);
 

@@ -271,6 +271,9 @@ def check_support_and_order(ttv):
     s, v, sh = ttv(subs, vals, (3, 3, 2), [0], [np.array([1.0, 10.0, 100.0])])
     assert [tuple(r) for r in s] == [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0), (2, 1)]
     assert list(v) == [4.0, 2.0, 500.0, -500.0, 10.0, 30.0]
+    # a lone infinity stays infinite (the compensation must not make it nan)
+    s, v, sh = ttv(np.array([[0, 0], [0, 1]], dtype=np.int64), np.array([float("inf"), 1.0]), (1, 2), [1], [np.ones(2)])
+    assert v[0] == float("inf")
     # compensated summation: 1e16 + 1 - 1e16 in one group is exactly 1
     subs = np.array([[0, 0], [0, 1], [0, 2]], dtype=np.int64)
     s, v, sh = ttv(subs, np.array([1e16, 1.0, -1e16]), (1, 3), [1], [np.ones(3)])

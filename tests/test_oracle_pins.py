@@ -54,3 +54,13 @@ def test_duplicates_summed_in_input_order():
     from fractions import Fraction
     exact = Fraction(0.1) + Fraction(0.2) + Fraction(0.3)
     assert v[0] == float(exact)
+
+
+def test_nonfinite_terms_follow_ieee_sum():
+    """Eq. 3 is a plain sum: one +inf term gives +inf, +inf and -inf give nan,
+    a nan term gives nan -- compensation must not change a non-finite sum."""
+    inf, nan = float("inf"), float("nan")
+    subs = np.array([[0, 0], [0, 1], [1, 0], [1, 1], [2, 0], [2, 1], [3, 0]], dtype=np.int64)
+    vals = np.array([inf, 1.0, inf, -inf, nan, 2.0, -inf])
+    s, v, _ = oracle.ttv(subs, vals, (4, 2), [1], [np.ones(2)])
+    assert v[0] == inf and np.isnan(v[1]) and np.isnan(v[2]) and v[3] == -inf
