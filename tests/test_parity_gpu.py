@@ -175,9 +175,14 @@ def test_nonfinite_inputs_propagate(cuda_lib):
     subs, vals, vecs = to_device(p)
     vals[5] = float("inf")
     vals[9] = float("nan")
+    ref, A = oracle_ttv(subs, vals, p.tensor.shape, p.modes, vecs)
     for accum in ("fp64", "exact"):
         r = cuda_lib.ttv_multi(subs, vals, p.tensor.shape, p.modes, vecs, accum=accum)
-        ref, _ = oracle_ttv(subs, vals, p.tensor.shape, p.modes, vecs)
         got = r.vals.cpu().numpy()
+        assert np.array_equal(r.subs.cpu().numpy(), ref[0])
         assert np.array_equal(np.isnan(got), np.isnan(ref[1]))
         assert np.array_equal(np.isinf(got), np.isinf(ref[1]))
+        fin = np.isfinite(ref[1])
+        assert np.array_equal(got[~fin & ~np.isnan(got)], ref[1][~fin & ~np.isnan(ref[1])])
+        err = np.abs(got[fin] - ref[1][fin])
+        assert np.all(err <= 1e-12 * np.maximum(np.abs(ref[1][fin]), 1e-3 * A[fin]))
