@@ -174,6 +174,33 @@ void ttv_out_free(ttv_out *out);
 /* Message for the calling thread's last error ("" if none). */
 const char *ttv_last_error(void);
 
+/* ---- allocation-free dense TTV ----------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory (code running under a host
+ * application that owns every allocation, a real-time loop that cannot take
+ * the allocator's locks or synchronisation, a process whose memory budget
+ * belongs to another runtime).  It computes the dense result (prod shape[R]
+ * binary64 values, row-major) into the caller's buffer `out` (out_len values)
+ * and allocates nothing: its scratch -- a status word and one partial array
+ * per CTA -- lives in a fixed device array of TTV_NOALLOC_SCRATCH_BYTES that
+ * is part of the library and stays resident on every GPU that loads it until
+ * the process exits.
+ *   - Limit: prod shape[R] <= 16384 cells (the dense path's shared-memory
+ *     accumulator); larger result spaces return TTV_ERR_UNSUPPORTED, and a
+ *     result larger than the fixed scratch returns TTV_ERR_BUDGET.
+ *   - vec_lens may be NULL; otherwise a mismatch returns TTV_ERR_VEC_LEN.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before capturing any stream.
+ *   - Synchronous: returns after `stream` has finished the call.
+ *   - Every call shares the one array (the status word is cleared at the start
+ *     of each call), so calls that overlap on the GPU -- on different streams
+ *     or from different host threads -- race and must be serialised. */
+#define TTV_NOALLOC_SCRATCH_BYTES (4u << 20)
+int ttv_dense_noalloc(const ttv_tensor *t, const int32_t *modes, int32_t n_v,
+                      const void *const *vecs, const int64_t *vec_lens, ttv_dtype v_dtype,
+                      double *out, int64_t out_len, ttv_stream_t stream);
+
 /* ---- measurement --------------------------------------------------------
  * Every kernel launch of the library is counted; with profiling enabled a
  * CUDA event pair brackets each launch on the launching stream.  The paper

@@ -310,3 +310,42 @@ def profile_names():
     buf = ctypes.create_string_buffer(max(1, need))
     lib.ttv_profile_names(buf, len(buf))
     return [x for x in buf.value.decode().split("\n") if x]
+
+
+# ---- allocation-free dense TTV -----------------------------------------------
+
+def ttv_dense_noalloc(subs: torch.Tensor, vals: torch.Tensor, shape, modes, vecs, out: torch.Tensor,
+                      stream=None) -> torch.Tensor:
+    """Dense-result TTV into ``out`` (a float64 CUDA buffer of at least
+    prod(shape[R]) values) without any device allocation by the library.
+
+    For callers that must not allocate (their host application owns all
+    device memory, or they run where the allocator's locks and
+    synchronisation are not allowed): the scratch is a fixed array inside the
+    library.  Synchronous; calls that overlap on the GPU race on that array,
+    so serialise them.  The first call on a device must precede any stream
+    capture.  Returns ``out[:prod].view(shape[R])``."""
+    lib = load()
+    if not getattr(lib, "_noalloc_declared", False):
+        P = ctypes.POINTER
+        lib.ttv_dense_noalloc.argtypes = [P(Tensor), P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_void_p),
+                                          P(ctypes.c_int64), ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p]
+        lib.ttv_dense_noalloc.restype = ctypes.c_int
+        lib._noalloc_declared = True
+    modes = [int(m) for m in modes]
+    if out.dtype != torch.float64 or not out.is_cuda or (out.numel() > 1 and out.stride(-1) != 1):
+        raise ValueError("out must be a contiguous float64 CUDA buffer")
+    vdt = vecs[0].dtype
+    t = make_tensor(subs, vals, shape)
+    m = (ctypes.c_int32 * len(modes))(*modes)
+    vp = (ctypes.c_void_p * len(vecs))(*[v.data_ptr() for v in vecs])
+    lens = (ctypes.c_int64 * len(vecs))(*[v.numel() for v in vecs])
+    rc = lib.ttv_dense_noalloc(ctypes.byref(t), m, len(modes), vp, lens, DTYPE[vdt], out.data_ptr(), out.numel(),
+                               _stream_handle(stream))
+    _check(lib, rc)
+    rshape = tuple(int(shape[i]) for i in range(len(shape)) if i not in modes)
+    n = 1
+    for x in rshape:
+        n *= x
+    return out.view(-1)[:n].view(rshape)

@@ -231,6 +231,22 @@ static int make_plan(const ttv_tensor* t, const int32_t* modes, int32_t n_v, con
     return TTV_OK;
 }
 
+// Validated stream descriptor of a dense-result call (the allocation-free
+// entry point in ttv_noalloc.cu builds its launch from this).
+int plan_dense_desc(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const void* const* vecs, ttv_dtype vd,
+                    const int64_t* vec_lens, StreamDesc* out) {
+    g_err.clear();
+    ttv_opts o;
+    memset(&o, 0, sizeof o);
+    o.fmt = TTV_OUT_DENSE;
+    o.path = TTV_PATH_DENSE;
+    Plan pl;
+    int rc = make_plan(t, modes, n_v, vecs, vd, vec_lens, &o, pl);
+    if (rc != TTV_OK) return rc;
+    *out = pl.desc;
+    return TTV_OK;
+}
+
 // Workspace layout; with a.base == nullptr it only measures.
 struct WsPtrs {
     Status* status;
