@@ -1,0 +1,221 @@
+// ttv_dense_vec.cu -- order-specialised dense accumulation kernel.
+//
+// Same computation as k_dense_accum (ttv_stream.cu), compiled per tensor
+// order D and subscript layout so that the per-mode loop is fully unrolled
+// with no runtime order checks, and every thread loads two consecutive
+// nonzeros per 16-byte access (one column element pair under the SoA layout,
+// two rows under AoS).  With kIntP the term is formed from exact integer
+// significand products (GB300's FP64 pipe issues ~1.7 operations per clock
+// per SM, so three binary64 multiplies per nonzero would cap the kernel below
+// the HBM rate); the accumulation is one binary64 add per nonzero into the
+// CTA's shared-memory array, as in the generic kernel.
+#include <algorithm>
+
+#include "ttv_internal.cuh"
+
+namespace ttv {
+
+constexpr int kVecThreads = 256;
+constexpr int kVecPairs = 2;       // pairs of nonzeros per thread per iteration
+
+template <int D, bool kIntP>
+__device__ __forceinline__ void dense_item(const StreamDesc& p, const double* sv, const SigEntry* sve,
+                                           const int64_t* s, double val, double* acc, uint32_t* pres,
+                                           int want_presence) {
+    bool good = true;
+#pragma unroll
+    for (int m = 0; m < D; ++m) good &= (uint64_t)s[m] < (uint64_t)p.shape[m];
+    if (!good) {
+        set_error(p.status, kErrSubscript);
+        return;
+    }
+    uint64_t key = 0;
+    double t;
+    if constexpr (kIntP) {
+        Sig a = decompose(val);
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+            if ((p.smask >> m) & 1u) sig_mul(a, sig_of(sve[p.voff[m] + s[m]]));
+            else key += (uint64_t)s[m] * p.kstride[m];
+        }
+        if (a.bad) {
+            double tt = val;
+#pragma unroll
+            for (int m = 0; m < D; ++m)
+                if ((p.smask >> m) & 1u)
+                    tt = tt * (p.vec_f32 ? (double)__ldg(static_cast<const float*>(p.vec[m]) + s[m])
+                                         : __ldg(static_cast<const double*>(p.vec[m]) + s[m]));
+            t = tt;
+        } else {
+            t = sig_to_double(a);
+        }
+    } else {
+        t = val;
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+            if ((p.smask >> m) & 1u) t = t * sv[p.voff[m] + s[m]];
+            else key += (uint64_t)s[m] * p.kstride[m];
+        }
+    }
+    atomicAdd(&acc[key], t);
+    if (want_presence) atomicOr(&pres[key >> 5], 1u << (key & 31));
+}
+
+template <int D, bool kSoA, bool kIntP>
+__global__ void __launch_bounds__(kVecThreads) k_dense_vec(StreamDesc p, int64_t chunk, int want_presence,
+                                                           size_t pres_off, size_t vec_off,
+                                                           double* __restrict__ partials,
+                                                           uint32_t* __restrict__ pres_partials) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    double* acc = reinterpret_cast<double*>(dsm);
+    uint32_t* pres = reinterpret_cast<uint32_t*>(dsm + pres_off);
+    double* sv = reinterpret_cast<double*>(dsm + vec_off);
+    SigEntry* sve = reinterpret_cast<SigEntry*>(dsm + vec_off);
+    const int64_t P = (int64_t)p.nkeys;
+    const int64_t npres = (P + 31) / 32;
+    for (int64_t i = threadIdx.x; i < P; i += kVecThreads) acc[i] = 0.0;
+    if (want_presence)
+        for (int64_t i = threadIdx.x; i < npres; i += kVecThreads) pres[i] = 0u;
+    if (kIntP) stage_vectors_sig(p, sve);
+    else stage_vectors(p, sv);
+    __syncthreads();
+
+    const int64_t lo = (int64_t)blockIdx.x * chunk;               // even
+    const int64_t hi = min(p.nnz, lo + chunk);
+    const int64_t npairs = hi > lo ? (hi - lo) / 2 : 0;            // whole pairs
+    const double* vd = static_cast<const double*>(p.vals);
+    const float* vf = static_cast<const float*>(p.vals);
+
+    for (int64_t q0 = threadIdx.x; q0 < npairs; q0 += (int64_t)kVecThreads * kVecPairs) {
+        int64_t s[kVecPairs][2][D];
+        double v[kVecPairs][2];
+        bool ok[kVecPairs];
+#pragma unroll
+        for (int u = 0; u < kVecPairs; ++u) {
+            const int64_t q = q0 + (int64_t)u * kVecThreads;
+            ok[u] = q < npairs;
+            if (!ok[u]) continue;
+            const int64_t k = lo + 2 * q;
+            if constexpr (kSoA) {
+#pragma unroll
+                for (int m = 0; m < D; ++m) {
+                    const longlong2 w = __ldcs(reinterpret_cast<const longlong2*>(p.subs + m * p.smode + k));
+                    s[u][0][m] = w.x;
+                    s[u][1][m] = w.y;
+                }
+            } else {
+                const longlong2* row = reinterpret_cast<const longlong2*>(p.subs + k * D);
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    const longlong2 w = __ldcs(row + j);
+                    const int e0 = 2 * j, e1 = 2 * j + 1;
+                    if (e0 < D) s[u][0][e0] = w.x; else s[u][1][e0 - D] = w.x;
+                    if (e1 < D) s[u][0][e1] = w.y; else s[u][1][e1 - D] = w.y;
+                }
+            }
+            if (p.val_f32) {
+                const float2 w = __ldcs(reinterpret_cast<const float2*>(vf + k));
+                v[u][0] = (double)w.x;
+                v[u][1] = (double)w.y;
+            } else {
+                const double2 w = __ldcs(reinterpret_cast<const double2*>(vd + k));
+                v[u][0] = w.x;
+                v[u][1] = w.y;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kVecPairs; ++u) {
+            if (!ok[u]) continue;
+            dense_item<D, kIntP>(p, sv, sve, s[u][0], v[u][0], acc, pres, want_presence);
+            dense_item<D, kIntP>(p, sv, sve, s[u][1], v[u][1], acc, pres, want_presence);
+        }
+    }
+    // odd tail of the last chunk
+    if (threadIdx.x == 0 && hi > lo && ((hi - lo) & 1)) {
+        const int64_t k = hi - 1;
+        int64_t s1[D];
+#pragma unroll
+        for (int m = 0; m < D; ++m) s1[m] = p.subs[k * p.snz + m * p.smode];
+        const double v1 = p.val_f32 ? (double)vf[k] : vd[k];
+        dense_item<D, kIntP>(p, sv, sve, s1, v1, acc, pres, want_presence);
+    }
+    __syncthreads();
+    double* my = partials + (size_t)blockIdx.x * P;
+    for (int64_t i = threadIdx.x; i < P; i += kVecThreads) my[i] = acc[i];
+    if (want_presence) {
+        uint32_t* mp = pres_partials + (size_t)blockIdx.x * npres;
+        for (int64_t i = threadIdx.x; i < npres; i += kVecThreads) mp[i] = pres[i];
+    }
+}
+
+// ---- host side ------------------------------------------------------------
+typedef void (*DenseVecKernel)(StreamDesc, int64_t, int, size_t, size_t, double*, uint32_t*);
+
+template <int D>
+static DenseVecKernel pick(bool soa, bool intp) {
+    if (soa) return intp ? k_dense_vec<D, true, true> : k_dense_vec<D, true, false>;
+    return intp ? k_dense_vec<D, false, true> : k_dense_vec<D, false, false>;
+}
+
+static DenseVecKernel dense_vec_kernel(int d, bool soa, bool intp) {
+    switch (d) {
+        case 2: return pick<2>(soa, intp);
+        case 3: return pick<3>(soa, intp);
+        case 4: return pick<4>(soa, intp);
+        case 5: return pick<5>(soa, intp);
+        case 6: return pick<6>(soa, intp);
+        default: return nullptr;
+    }
+}
+
+// Whether the specialised kernel applies: order 2..6, staged vectors, and
+// 16-byte aligned pairs under an SoA or AoS layout.
+bool dense_vec_applicable(const StreamDesc& p) {
+    if (p.d < 2 || p.d > 6 || !p.vec_smem) return false;
+    const uintptr_t sb = reinterpret_cast<uintptr_t>(p.subs), vb = reinterpret_cast<uintptr_t>(p.vals);
+    if ((sb & 15) || (vb & 15)) return false;
+    const bool soa = p.snz == 1 && (p.smode % 2 == 0);
+    const bool aos = p.snz == p.d && p.smode == 1;
+    return soa || aos;
+}
+
+int dense_vec_products_int(const StreamDesc& p) { return __builtin_popcount(p.smask) >= 2; }
+
+size_t dense_vec_smem(const StreamDesc& p, int want_presence) {
+    size_t off = (size_t)p.nkeys * sizeof(double);
+    if (want_presence) off += ((p.nkeys + 31) / 32) * sizeof(uint32_t);
+    off = (off + 15) & ~size_t(15);
+    off += (size_t)p.vtotal * (dense_vec_products_int(p) ? sizeof(SigEntry) : sizeof(double));
+    return off;
+}
+
+int dense_vec_grid(const StreamDesc& p, int want_presence) {
+    const bool soa = p.snz == 1;
+    DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p));
+    const size_t smem = dense_vec_smem(p, want_presence);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kVecThreads, smem);
+    per_sm = std::max(1, std::min(per_sm, 4));
+    const int64_t min_chunk = std::max<int64_t>((int64_t)kVecThreads * kVecPairs * 2 * 4, (int64_t)p.nkeys * 4);
+    const int64_t by_work = std::max<int64_t>(1, (p.nnz + min_chunk - 1) / min_chunk);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(by_work, (int64_t)num_sms() * per_sm));
+}
+
+void launch_dense_vec(const StreamDesc& p, int want_presence, int G, double* partials, uint32_t* pres_partials,
+                      cudaStream_t stream) {
+    const bool soa = p.snz == 1;
+    DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p));
+    const size_t smem = dense_vec_smem(p, want_presence);
+    size_t pres_off = (size_t)p.nkeys * sizeof(double);
+    size_t vec_off = pres_off + (want_presence ? ((p.nkeys + 31) / 32) * sizeof(uint32_t) : 0);
+    vec_off = (vec_off + 15) & ~size_t(15);
+    int64_t chunk = (p.nnz + G - 1) / G;
+    chunk = (chunk + 1) & ~int64_t(1);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+    TTV_LAUNCH("dense_accum", stream,
+               k<<<G, kVecThreads, smem, stream>>>(p, chunk, want_presence, pres_off, vec_off, partials,
+                                                   pres_partials));
+}
+
+}  // namespace ttv

@@ -230,7 +230,14 @@ __global__ void __launch_bounds__(1024) k_compact_cells(StreamDesc p, const doub
 
 size_t dense_smem_bytes(const StreamDesc& p, int want_presence) { return dense_layout(p, want_presence).total; }
 
+// order-specialised kernel (ttv_dense_vec.cu)
+bool dense_vec_applicable(const StreamDesc& p);
+int dense_vec_grid(const StreamDesc& p, int want_presence);
+void launch_dense_vec(const StreamDesc& p, int want_presence, int G, double* partials, uint32_t* pres_partials,
+                      cudaStream_t stream);
+
 int dense_grid(const StreamDesc& p, int want_presence) {
+    if (dense_vec_applicable(p)) return dense_vec_grid(p, want_presence);
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -255,7 +262,9 @@ void launch_dense(const StreamDesc& p, int want_presence, int compensated, int G
                   uint32_t* pres_partials, double* cell_vals, uint32_t* cell_flags, cudaStream_t stream) {
     const DenseSmemLayout L = dense_layout(p, want_presence);
     const int64_t chunk = std::max<int64_t>(1, (p.nnz + G - 1) / G);
-    if (use_int_products(p)) {
+    if (dense_vec_applicable(p)) {
+        launch_dense_vec(p, want_presence, G, partials, pres_partials, stream);
+    } else if (use_int_products(p)) {
         cudaFuncSetAttribute(k_dense_accum<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(L.total, 1));
         TTV_LAUNCH("dense_accum", stream, k_dense_accum<true><<<G, kStreamThreads, L.total, stream>>>(
                                               p, chunk, want_presence, L.pres_off, L.vec_off, partials, pres_partials));
