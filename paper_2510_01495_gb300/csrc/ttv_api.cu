@@ -30,6 +30,11 @@ void launch_seg_reduce(const uint64_t* keys, const double* vals, int64_t n, uint
                        unsigned long long* lookback, uint32_t* ticket, uint32_t* long_list, const StreamDesc& p,
                        const SegOut& o, Status* st, cudaStream_t stream);
 
+bool bucket_applicable(const StreamDesc& p);
+size_t bucket_workspace_bytes(int64_t nnz, int key_bits);
+void launch_bucket(const StreamDesc& p, int key_bits, void* ws, int64_t* out_subs, double* out_vals,
+                   int64_t cap_rows, cudaStream_t stream);
+
 constexpr int64_t kDenseMaxCells = 16384;       // key spaces accumulated in shared memory
 constexpr size_t kVecSmemMax = 64 * 1024;       // staged vector bytes per CTA
 constexpr int64_t kMaxSortN = (1ll << 30) - 1;  // 30-bit counts in the look-back words
@@ -87,6 +92,7 @@ struct OutState {
     int dense_out = 0;
     int finalized = 0;
     int nonfinite = 0;          // fixed-point path met inf/nan: rerun in binary64
+    int retry_sort = 0;         // bucket path gave up: rerun on the sort path
     int rc = TTV_OK;
 };
 
@@ -136,7 +142,8 @@ static int bits_for(uint64_t nkeys) {
 }
 
 static int make_plan(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const void* const* vecs,
-                     ttv_dtype vd, const int64_t* vec_lens, const ttv_opts* o, Plan& pl, bool force_fp64 = false) {
+                     ttv_dtype vd, const int64_t* vec_lens, const ttv_opts* o, Plan& pl, bool force_fp64 = false,
+                     bool force_sort = false) {
     if (!t || !o) return fail(TTV_ERR_ARG, "null tensor or options");
     if (t->d < 1 || t->d > TTV_MAX_D) return fail(TTV_ERR_ARG, "order d=%d outside 1..%d", t->d, TTV_MAX_D);
     if (t->nnz < 0) return fail(TTV_ERR_ARG, "negative nnz");
@@ -189,6 +196,7 @@ static int make_plan(const ttv_tensor* t, const int32_t* modes, int32_t n_v, con
         if (nk > (unsigned __int128)UINT64_MAX) return fail(TTV_ERR_KEY_OVERFLOW, "prod of surviving mode sizes exceeds 2^64-1");
     }
     p.nkeys = (uint64_t)nk;
+    for (int j = 0; j < p.nr; ++j) udiv_magic((uint64_t)p.rshape[j], p.rmagic[j], p.rsh[j]);
     // vectors staged in shared memory when they fit
     int64_t vt = 0;
     for (int m = 0; m < t->d; ++m)
@@ -204,8 +212,13 @@ static int make_plan(const ttv_tensor* t, const int32_t* modes, int32_t n_v, con
     int path = o->path;
     const bool dense_ok = (int64_t)p.nkeys <= kDenseMaxCells;
     const bool want_exact = o->accum == TTV_ACCUM_EXACT || o->deterministic;
-    if (path == TTV_PATH_AUTO) path = (dense_ok || pl.order0) ? TTV_PATH_DENSE : TTV_PATH_SORT;
-    if (path == TTV_PATH_HASH || path == TTV_PATH_BUCKET) path = TTV_PATH_SORT;   // not built yet: sort
+    if (path == TTV_PATH_AUTO) {
+        if (dense_ok || pl.order0) path = TTV_PATH_DENSE;
+        else path = TTV_PATH_SORT;   // the bucket path is selectable; it does not beat the sort path yet
+    }
+    if (path == TTV_PATH_HASH) path = TTV_PATH_SORT;   // not built yet: sort
+    if (path == TTV_PATH_BUCKET && (pl.dense_out || !bucket_applicable(p))) path = TTV_PATH_SORT;
+    if (force_sort && path == TTV_PATH_BUCKET) path = TTV_PATH_SORT;
     if (path == TTV_PATH_DENSE && !dense_ok) return fail(TTV_ERR_UNSUPPORTED, "dense path needs prod shape[R] <= %lld", (long long)kDenseMaxCells);
     if (path == TTV_PATH_DENSE) {
         // exact fixed point when asked for determinism (binary64 shared-memory
@@ -215,7 +228,8 @@ static int make_plan(const ttv_tensor* t, const int32_t* modes, int32_t n_v, con
         pl.use_fx = want_exact && pl.fx.ok && !force_fp64 && p.nnz > 0;
         if (want_exact && !pl.fx.ok && !pl.order0 && p.nnz > 0) path = TTV_PATH_SORT;
     }
-    if (path == TTV_PATH_SORT && p.nnz > kMaxSortN) return fail(TTV_ERR_UNSUPPORTED, "sort path supports nnz < 2^30");
+    if ((path == TTV_PATH_SORT || path == TTV_PATH_BUCKET) && p.nnz > kMaxSortN)
+        return fail(TTV_ERR_UNSUPPORTED, "sparse accumulation supports nnz < 2^30");
     pl.path = path;
     pl.want_presence = (path == TTV_PATH_DENSE) && !pl.dense_out;
 
@@ -250,6 +264,8 @@ int plan_dense_desc(const ttv_tensor* t, const int32_t* modes, int32_t n_v, cons
 // Workspace layout; with a.base == nullptr it only measures.
 struct WsPtrs {
     Status* status;
+    // bucket
+    void* bucket_ws;
     // dense
     void* fx_ws;
     double* partials;
@@ -280,6 +296,8 @@ static void layout(const Plan& pl, Arena& a, WsPtrs& w) {
             w.cell_vals = a.take<double>(P);
             w.cell_flags = a.take<uint32_t>(P);
         }
+    } else if (pl.path == TTV_PATH_BUCKET) {
+        w.bucket_ws = a.take<char>(bucket_workspace_bytes(p.nnz, pl.key_bits));
     } else {
         const int64_t n = std::max<int64_t>(p.nnz, 1);
         const int npass = (pl.key_bits + 7) / 8;
@@ -321,6 +339,10 @@ static int finalize(ttv_out* out) {
     if (h.err & kErrTimeout) return s->rc = fail(TTV_ERR_TIMEOUT, "a bounded device wait ran out");
     if (h.err & kErrCapacity) return s->rc = fail(TTV_ERR_CAPACITY, "result (%llu rows) exceeds the output buffer", (unsigned long long)h.nnz_out);
     if (h.err & kErrInternal) return s->rc = fail(TTV_ERR_CUDA, "internal device check failed");
+    if (h.err & kErrRetry) {
+        s->retry_sort = 1;
+        return s->rc = fail(TTV_ERR_UNSUPPORTED, "bucket path could not place every pair");
+    }
     if (h.err & kErrNonFinite) {
         s->nonfinite = 1;
         return s->rc = fail(TTV_ERR_UNSUPPORTED, "non-finite input on the fixed-point dense path");
@@ -396,6 +418,8 @@ static int execute(const Plan& pl, ttv_out* out, const ttv_opts* o, cudaStream_t
             launch_dense(p, pl.want_presence, pl.compensated, pl.grid, w.partials, w.pres_partials, cell_vals,
                          w.cell_flags, stream);
         if (pl.want_presence) launch_compact_cells(p, w.cell_vals, w.cell_flags, cap_rows_eff, out->subs, ovals, stream);
+    } else if (pl.path == TTV_PATH_BUCKET) {
+        launch_bucket(p, pl.key_bits, w.bucket_ws, out->subs, ovals, cap_rows_eff, stream);
     } else {
         launch_keys_terms(p, w.sb.keys[0], w.sb.vals[0], stream);
         SortBuffers sb = w.sb;
@@ -464,10 +488,12 @@ int ttv_multi_checked(const ttv_tensor* t, const int32_t* modes, int32_t n_v, co
     if (rc != TTV_OK) return rc;
     rc = execute(pl, out, o, reinterpret_cast<cudaStream_t>(stream));
     OutState* s = static_cast<OutState*>(out->internal);
-    if (rc == TTV_ERR_UNSUPPORTED && s && s->nonfinite) {
-        // inf or nan in the input: the binary64 kernel propagates them like the definition
+    if (rc == TTV_ERR_UNSUPPORTED && s && (s->nonfinite || s->retry_sort)) {
+        // inf or nan in the input: the binary64 kernel propagates them like the
+        // definition; a bucket overflow: the sort path has no capacity limits
         Plan p2;
-        rc = make_plan(t, modes, n_v, vecs, v_dtype, vec_lens, o, p2, /*force_fp64=*/true);
+        rc = make_plan(t, modes, n_v, vecs, v_dtype, vec_lens, o, p2, /*force_fp64=*/s->nonfinite != 0,
+                       /*force_sort=*/s->retry_sort != 0);
         if (rc != TTV_OK) return rc;
         void* keep_subs = s->owned_subs;
         void* keep_vals = s->owned_vals;

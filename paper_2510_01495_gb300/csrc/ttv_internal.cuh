@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/ttv.h"
+#include "ttv_udiv.h"
 
 namespace ttv {
 
@@ -19,6 +20,7 @@ enum : uint32_t {
     kErrCapacity = 1u << 2,    // result larger than the output buffer
     kErrInternal = 1u << 3,    // an internal invariant failed (bucket overflow ...)
     kErrNonFinite = 1u << 4,   // inf/nan met by a fixed-point accumulator
+    kErrRetry = 1u << 5,       // bucket path gave up (skewed sample): rerun on the sort path
 };
 
 // Per-call device status block (lives in the call's workspace).
@@ -52,8 +54,12 @@ struct StreamDesc {
     uint64_t nkeys;                   // prod shape[R] (key space size)
     int32_t rmode[kMaxD];             // surviving modes, ascending
     int64_t rshape[kMaxD];            // shape of the result
+    uint64_t rmagic[kMaxD];           // division by rshape[j] (see udiv_invariant)
+    uint32_t rsh[kMaxD];              // shift pair: sh1 | sh2 << 8
     Status* status;
 };
+
+
 
 __device__ __forceinline__ void set_error(Status* st, uint32_t bit) {
     atomicOr(&st->err, bit);
@@ -268,12 +274,14 @@ __device__ __forceinline__ bool key_term_sig(const StreamDesc& p, const SigEntry
     return good;
 }
 
-// Inverse of the linearisation: key -> result subscripts (row-major over R).
+// Inverse of the linearisation: key -> result subscripts (row-major over R),
+// with multiply-high division by the invariant mode sizes.
 __device__ __forceinline__ void delinearise(const StreamDesc& p, uint64_t key, int64_t* out_row) {
     for (int j = p.nr - 1; j >= 0; --j) {
         const uint64_t n = (uint64_t)p.rshape[j];
-        out_row[j] = (int64_t)(key % n);
-        key /= n;
+        const uint64_t q = udiv_invariant(key, p.rmagic[j], p.rsh[j]);
+        out_row[j] = (int64_t)(key - q * n);
+        key = q;
     }
 }
 

@@ -186,3 +186,79 @@ def test_nonfinite_inputs_propagate(cuda_lib):
         assert np.array_equal(got[~fin & ~np.isnan(got)], ref[1][~fin & ~np.isnan(ref[1])])
         err = np.abs(got[fin] - ref[1][fin])
         assert np.all(err <= 1e-12 * np.maximum(np.abs(ref[1][fin]), 1e-3 * A[fin]))
+
+
+# ---- bucket path (splitter partition + on-chip sort) ------------------------------
+
+@pytest.mark.parametrize("layout", ["soa", "aos"])
+def test_bucket_path_zipf(cuda_lib, layout):
+    shape = (2000, 500, 10000, 200, 50)
+    p = S.single_5way_zipf(nnz=400_000, shape=shape)
+    run_case(cuda_lib, p, path="bucket", layout=layout)
+
+
+def test_bucket_path_large_uniform(cuda_lib):
+    # 1.5e6 uniform nonzeros, 3-way result of 1.2e9 cells
+    p = rand_problem(77, (1000, 1200, 50, 1000), 1_500_000, [2])
+    run_case(cuda_lib, p, path="bucket", layout="soa")
+    run_case(cuda_lib, p, layout="soa")
+
+
+def test_bucket_heavy_keys_and_oversized_buckets(cuda_lib):
+    # 40 surviving tuples carry half of 600k nonzeros (7.5k each): heavy keys that
+    # the sample isolates, or buckets larger than the on-chip capacity that are
+    # split by key sub-ranges; the rest is spread thinly
+    g = np.random.default_rng(9)
+    n = 600_000
+    s0 = g.integers(0, 50, n)
+    s1 = g.integers(0, 1000, n)
+    s2 = g.integers(0, 2000, n)
+    heavy = g.integers(0, 40, n // 2)
+    s0[: n // 2] = heavy % 50
+    s2[: n // 2] = (heavy * 37) % 2000
+    perm = g.permutation(n)
+    subs = np.stack([s0, s1, s2], axis=1)[perm]
+    vals = g.uniform(-1, 1, n)
+    x = g.uniform(-1, 1, 1000)
+    p = S.Problem(S.SparseTensor(torch.from_numpy(subs), torch.from_numpy(vals), (50, 1000, 2000)), [1],
+                  [torch.from_numpy(x)], name="bucket_heavy")
+    run_case(cuda_lib, p, path="bucket", layout="soa")
+    run_case(cuda_lib, p, path="bucket", layout="aos")
+
+
+def test_bucket_dense_cluster_split(cuda_lib):
+    # 200k distinct keys packed into a narrow key range next to a sparse tail:
+    # quantile buckets are uneven and some exceed the on-chip capacity
+    g = np.random.default_rng(11)
+    n = 300_000
+    lin = np.concatenate([g.choice(250_000, size=250_000, replace=False),
+                          g.integers(0, 10**12, 50_000)])
+    shape = (10**6, 10**6, 7)
+    s0 = lin // 10**6
+    s1 = lin % 10**6
+    s2 = g.integers(0, 7, n)
+    subs = np.stack([s0, s1, s2], axis=1)[g.permutation(n)]
+    vals = g.uniform(-1, 1, n)
+    x = g.uniform(-1, 1, 7)
+    p = S.Problem(S.SparseTensor(torch.from_numpy(subs), torch.from_numpy(vals), shape), [2],
+                  [torch.from_numpy(x)], name="bucket_cluster")
+    run_case(cuda_lib, p, path="bucket", layout="soa")
+
+
+def test_bucket_near_heavy_keys_at_range_top(cuda_lib):
+    # keys repeated just under one quantile step (~4k times) are not isolated and
+    # end up at the top of an oversized bucket's key range
+    g = np.random.default_rng(21)
+    nh = 60
+    mult = g.integers(3000, 4090, nh)
+    heavy_keys = g.choice(5_000_000, size=nh, replace=False)
+    lin = np.concatenate([np.repeat(heavy_keys, mult), g.integers(0, 5_000_000, 400_000)])
+    n = lin.size
+    s0, s2 = lin // 1000, lin % 1000
+    s1 = g.integers(0, 30, n)
+    subs = np.stack([s0, s1, s2], axis=1)[g.permutation(n)]
+    vals = g.uniform(-1, 1, n)
+    x = g.uniform(-1, 1, 30)
+    p = S.Problem(S.SparseTensor(torch.from_numpy(subs), torch.from_numpy(vals), (5000, 30, 1000)), [1],
+                  [torch.from_numpy(x)], name="bucket_near_heavy")
+    run_case(cuda_lib, p, path="bucket", layout="soa")
