@@ -174,6 +174,80 @@ void ttv_out_free(ttv_out *out);
 /* Message for the calling thread's last error ("" if none). */
 const char *ttv_last_error(void);
 
+/* ---- batched TTV ------------------------------------------------------------
+ * Many independent TTVs (paper Eq. 3 each) in one CUDA-graph launch.  The
+ * first call with a given set of problems captures every problem's kernels
+ * into one graph, spread over up to 8 concurrent streams (largest problems
+ * first), and instantiates it; a later call with identical problems (same
+ * pointers, sizes, modes, output buffers, workspace and options) launches the
+ * cached graph without host work per problem.  Up to 16 graphs are cached;
+ * ttv_batch_release() drops them. */
+typedef struct {
+    ttv_tensor tensor;
+    const int32_t *modes;        /* host, n_v contracted modes                    */
+    int32_t n_v;
+    const void *const *vecs;     /* host array of n_v device vectors              */
+    ttv_dtype v_dtype;
+} ttv_problem;
+
+/* outs[i] must point at caller buffers (subs/vals with capacities, see
+ * ttv_out_capacity); opts->workspace may hold ttv_batch_workspace_size()
+ * bytes (else the library allocates one block and keeps it with the cached
+ * graph).  Synchronous unless opts->async (then ttv_out_sync each result).
+ * Results of a cached graph are rewritten by its next launch.  A problem that
+ * fails leaves its error in ttv_out_sync(&outs[i]); the call returns the
+ * first failure. */
+int ttv_batch(const ttv_problem *probs, int32_t n, ttv_out *outs, const ttv_opts *opts,
+              ttv_stream_t stream);
+int ttv_batch_workspace_size(const ttv_problem *probs, int32_t n, const ttv_opts *opts, size_t *bytes);
+/* Kernel launches one replay of the graph for these problems performs (0 if
+ * it is not cached). */
+long long ttv_batch_graph_launches(const ttv_problem *probs, int32_t n, const ttv_out *outs, const ttv_opts *opts);
+void ttv_batch_release(void);
+
+/* ---- serving ------------------------------------------------------------------
+ * A continuous-batching TTV server.  Registered tensors stay resident in
+ * server-owned device memory.  Requests (contracted modes + host vectors)
+ * queue up; a scheduler thread admits any queued request for which a stream
+ * slot is free and the memory budget covers its workspace, result and
+ * vectors (a request that does not fit yet does not block smaller ones behind
+ * it), so the work of several requests overlaps on the GPU.  Latency is
+ * measured from submit to completion on the GPU.  Results are
+ * library-allocated device buffers handed over by ttv_server_wait (release
+ * with ttv_out_free); they stop counting against the budget once complete. */
+typedef struct ttv_server ttv_server;
+
+typedef struct {
+    double p50_us, p99_us, mean_us, max_us;   /* submit -> completion latency    */
+    long long completed, admitted, refused, pending;
+    double seconds;                           /* since creation or reset          */
+    double throughput_rps, throughput_gnnz_s; /* completed requests / nonzeros    */
+    size_t bytes_in_use, budget_bytes;
+} ttv_stats;
+
+/* budget_bytes bounds resident tensors + in-flight requests; n_slots (1..64)
+ * concurrent requests, one CUDA stream each. */
+int ttv_server_create(size_t budget_bytes, int32_t n_slots, ttv_server **server);
+/* Copies a device tensor (any subscript strides) into the server; it counts
+ * against the budget until the server is destroyed.  TTV_ERR_BUDGET if it
+ * does not fit. */
+int ttv_server_register(ttv_server *server, const ttv_tensor *t, int32_t *tensor_id);
+/* Queues a TTV of registered tensor `tensor_id` with n_v host vectors (each
+ * shape[modes[i]] entries of v_dtype, copied at submit).  opts may be NULL
+ * (its workspace and async fields are ignored).  TTV_ERR_BUDGET if the request
+ * could never fit next to the resident tensors. */
+int ttv_server_submit(ttv_server *server, int32_t tensor_id, const int32_t *modes, int32_t n_v,
+                      const void *const *host_vecs, ttv_dtype v_dtype, const ttv_opts *opts,
+                      uint64_t *req_id);
+/* Waits up to timeout_us (< 0: forever) for a request and moves its result
+ * into *out.  TTV_ERR_TIMEOUT if it is not done in time. */
+int ttv_server_wait(ttv_server *server, uint64_t req_id, int64_t timeout_us, ttv_out *out);
+int ttv_server_stats(ttv_server *server, ttv_stats *stats);
+/* Clears latencies and counters (e.g. after a warm-up). */
+int ttv_server_reset_stats(ttv_server *server);
+/* Drains running requests, then frees everything the server owns. */
+void ttv_server_destroy(ttv_server *server);
+
 /* ---- allocation-free dense TTV ----------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that must not allocate device memory (code running under a host

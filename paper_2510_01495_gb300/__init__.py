@@ -349,3 +349,226 @@ def ttv_dense_noalloc(subs: torch.Tensor, vals: torch.Tensor, shape, modes, vecs
     for x in rshape:
         n *= x
     return out.view(-1)[:n].view(rshape)
+
+
+# ---- batched TTV (one CUDA graph per set of problems) ------------------------
+
+class Problem(ctypes.Structure):
+    _fields_ = [("tensor", Tensor), ("modes", ctypes.POINTER(ctypes.c_int32)), ("n_v", ctypes.c_int32),
+                ("vecs", ctypes.POINTER(ctypes.c_void_p)), ("v_dtype", ctypes.c_int)]
+
+
+def _declare_batch(lib):
+    if getattr(lib, "_batch_declared", False):
+        return lib
+    P = ctypes.POINTER
+    lib.ttv_batch.argtypes = [P(Problem), ctypes.c_int32, P(Out), P(Opts), ctypes.c_void_p]
+    lib.ttv_batch.restype = ctypes.c_int
+    lib.ttv_batch_workspace_size.argtypes = [P(Problem), ctypes.c_int32, P(Opts), P(ctypes.c_size_t)]
+    lib.ttv_batch_workspace_size.restype = ctypes.c_int
+    lib.ttv_batch_graph_launches.argtypes = [P(Problem), ctypes.c_int32, P(Out), P(Opts)]
+    lib.ttv_batch_graph_launches.restype = ctypes.c_longlong
+    lib.ttv_batch_release.argtypes = []
+    lib.ttv_batch_release.restype = None
+    lib._batch_declared = True
+    return lib
+
+
+class Batch:
+    """Many TTVs run as one CUDA-graph launch (``ttv_batch``).
+
+    ``problems`` is a list of ``(subs, vals, shape, modes, vecs)`` on the
+    device.  Result and workspace buffers are allocated once here, so every
+    ``run()`` after the first replays the cached graph."""
+
+    def __init__(self, problems, fmt="sparse", path="auto", accum="fp64"):
+        self.lib = _declare_batch(load())
+        self.n = len(problems)
+        self._keep = []
+        self.probs = (Problem * max(1, self.n))()
+        self.fmt = fmt
+        self.meta = []
+        for i, (subs, vals, shape, modes, vecs) in enumerate(problems):
+            t = make_tensor(subs, vals, shape)
+            m = (ctypes.c_int32 * len(modes))(*[int(x) for x in modes])
+            vp = (ctypes.c_void_p * len(vecs))(*[v.data_ptr() for v in vecs])
+            self.probs[i] = Problem(t, ctypes.cast(m, ctypes.POINTER(ctypes.c_int32)), len(modes),
+                                    ctypes.cast(vp, ctypes.POINTER(ctypes.c_void_p)), DTYPE[vecs[0].dtype])
+            self._keep.append((t, m, vp, subs, vals, vecs))
+            rows, nvals = out_capacity(subs, vals, shape, list(modes), fmt=fmt, path=path, accum=accum)
+            order = len(shape) - len(modes)
+            ov = torch.empty(max(1, nvals), dtype=torch.float64, device=subs.device)
+            os_ = (torch.empty((max(1, rows), order), dtype=torch.int64, device=subs.device)
+                   if fmt != "dense" and order > 0 else None)
+            self.meta.append((ov, os_, tuple(shape), list(modes)))
+        self.opts0 = make_opts(fmt=fmt, path=path, accum=accum)
+        nbytes = ctypes.c_size_t()
+        _check(self.lib, self.lib.ttv_batch_workspace_size(self.probs, self.n, ctypes.byref(self.opts0),
+                                                           ctypes.byref(nbytes)))
+        dev = problems[0][0].device if problems else torch.device("cuda")
+        self.workspace = torch.empty(max(1, nbytes.value), dtype=torch.uint8, device=dev)
+        self.opts = make_opts(fmt=fmt, path=path, accum=accum, workspace=self.workspace)
+
+    def _outs(self):
+        outs = (Out * max(1, self.n))()
+        for i, (ov, os_, _, _) in enumerate(self.meta):
+            outs[i].vals = ov.data_ptr()
+            outs[i].vals_capacity = ov.numel()
+            if os_ is not None:
+                outs[i].subs = os_.data_ptr()
+                outs[i].subs_capacity = os_.shape[0]
+        return outs
+
+    def run(self, stream=None):
+        """Launch the batch; returns one Result per problem (views of the
+        batch's buffers, rewritten by the next run)."""
+        outs = self._outs()
+        rc = self.lib.ttv_batch(self.probs, self.n, outs, ctypes.byref(self.opts), _stream_handle(stream))
+        try:
+            _check(self.lib, rc)
+            res = []
+            for i, (ov, os_, shape, modes) in enumerate(self.meta):
+                newshape = tuple(int(outs[i].shape[j]) for j in range(outs[i].order))
+                nn = int(outs[i].nnz)
+                if outs[i].is_dense:
+                    res.append(Result(None, ov[:nn].view(newshape), newshape, True))
+                else:
+                    subs_out = os_[:nn] if os_ is not None else torch.zeros((nn, 0), dtype=torch.int64, device=ov.device)
+                    res.append(Result(subs_out, ov[:nn], newshape, False))
+            return res
+        finally:
+            for i in range(self.n):
+                self.lib.ttv_out_free(ctypes.byref(outs[i]))
+
+    def graph_launches(self) -> int:
+        """Kernel launches one replay of the cached graph performs."""
+        return int(self.lib.ttv_batch_graph_launches(self.probs, self.n, self._outs(), ctypes.byref(self.opts)))
+
+
+def batch_release():
+    """Drops every cached batch graph."""
+    _declare_batch(load()).ttv_batch_release()
+
+
+# ---- serving (continuous batching) ------------------------------------------
+
+class Stats(ctypes.Structure):
+    _fields_ = [("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("completed", ctypes.c_longlong), ("admitted", ctypes.c_longlong),
+                ("refused", ctypes.c_longlong), ("pending", ctypes.c_longlong), ("seconds", ctypes.c_double),
+                ("throughput_rps", ctypes.c_double), ("throughput_gnnz_s", ctypes.c_double),
+                ("bytes_in_use", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t)]
+
+
+def _declare_serve(lib):
+    if getattr(lib, "_serve_declared", False):
+        return lib
+    P = ctypes.POINTER
+    lib.ttv_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int32, P(ctypes.c_void_p)]
+    lib.ttv_server_create.restype = ctypes.c_int
+    lib.ttv_server_register.argtypes = [ctypes.c_void_p, P(Tensor), P(ctypes.c_int32)]
+    lib.ttv_server_register.restype = ctypes.c_int
+    lib.ttv_server_submit.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int32), ctypes.c_int32,
+                                      P(ctypes.c_void_p), ctypes.c_int, P(Opts), P(ctypes.c_uint64)]
+    lib.ttv_server_submit.restype = ctypes.c_int
+    lib.ttv_server_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, P(Out)]
+    lib.ttv_server_wait.restype = ctypes.c_int
+    lib.ttv_server_stats.argtypes = [ctypes.c_void_p, P(Stats)]
+    lib.ttv_server_stats.restype = ctypes.c_int
+    lib.ttv_server_reset_stats.argtypes = [ctypes.c_void_p]
+    lib.ttv_server_reset_stats.restype = ctypes.c_int
+    lib.ttv_server_destroy.argtypes = [ctypes.c_void_p]
+    lib.ttv_server_destroy.restype = None
+    lib._serve_declared = True
+    return lib
+
+
+class _DeviceArray:
+    """Zero-copy view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 2, "strides": None}
+
+
+def _take_result(lib, out: Out) -> Result:
+    """Copies a library-owned result into torch tensors and releases it."""
+    try:
+        newshape = tuple(int(out.shape[j]) for j in range(out.order))
+        n = int(out.nnz)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if n > 0 and out.vals:
+            vals = torch.as_tensor(_DeviceArray(out.vals, (n,), "<f8"), device=dev).clone()
+        else:
+            vals = torch.zeros(n, dtype=torch.float64, device=dev)
+        if out.is_dense:
+            return Result(None, vals.view(newshape), newshape, True)
+        if out.order > 0 and n > 0 and out.subs:
+            subs = torch.as_tensor(_DeviceArray(out.subs, (n, out.order), "<i8"), device=dev).clone()
+        else:
+            subs = torch.zeros((n, out.order), dtype=torch.int64, device=dev)
+        return Result(subs, vals, newshape, False)
+    finally:
+        lib.ttv_out_free(ctypes.byref(out))
+
+
+class Server:
+    """Continuous-batching TTV server (``ttv_server_*``): resident tensors,
+    requests admitted by memory budget onto ``slots`` concurrent streams."""
+
+    def __init__(self, budget_bytes: int, slots: int = 8):
+        self.lib = _declare_serve(load())
+        self.h = ctypes.c_void_p()
+        _check(self.lib, self.lib.ttv_server_create(int(budget_bytes), int(slots), ctypes.byref(self.h)))
+        self.shapes = {}
+
+    def register(self, subs, vals, shape) -> int:
+        t = make_tensor(subs, vals, shape)
+        tid = ctypes.c_int32()
+        _check(self.lib, self.lib.ttv_server_register(self.h, ctypes.byref(t), ctypes.byref(tid)))
+        self.shapes[int(tid.value)] = tuple(shape)
+        torch.cuda.synchronize()
+        return int(tid.value)
+
+    def submit(self, tensor_id: int, modes, host_vecs, fmt="sparse", accum="fp64", path="auto") -> int:
+        import numpy as np
+        arrs = [np.ascontiguousarray(v) for v in host_vecs]
+        dt = arrs[0].dtype
+        if any(a.dtype != dt for a in arrs) or dt not in (np.float64, np.float32):
+            raise TypeError("host vectors must all be float64 or all float32")
+        m = (ctypes.c_int32 * len(modes))(*[int(x) for x in modes])
+        vp = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+        o = make_opts(fmt=fmt, accum=accum, path=path)
+        rid = ctypes.c_uint64()
+        _check(self.lib, self.lib.ttv_server_submit(self.h, int(tensor_id), m, len(arrs), vp,
+                                                    1 if dt == np.float32 else 0, ctypes.byref(o), ctypes.byref(rid)))
+        return int(rid.value)
+
+    def wait(self, req_id: int, timeout_us: int = -1) -> Result:
+        out = Out()
+        rc = self.lib.ttv_server_wait(self.h, int(req_id), int(timeout_us), ctypes.byref(out))
+        if rc != 0:
+            msg = self.lib.ttv_last_error().decode(errors="replace")
+            if out.internal:
+                self.lib.ttv_out_free(ctypes.byref(out))
+            raise TTVError(rc, msg)
+        return _take_result(self.lib, out)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self.lib, self.lib.ttv_server_stats(self.h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def reset_stats(self):
+        _check(self.lib, self.lib.ttv_server_reset_stats(self.h))
+
+    def close(self):
+        if self.h:
+            self.lib.ttv_server_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

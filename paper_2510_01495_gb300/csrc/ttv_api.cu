@@ -71,6 +71,16 @@ class StatusPool {
         free_.pop_back();
         return s;
     }
+    // Ensures n free slots (pinned allocations are not allowed inside a capture).
+    bool reserve(size_t n) {
+        std::lock_guard<std::mutex> g(mu_);
+        while (free_.size() < n) {
+            Status* chunk = nullptr;
+            if (cudaHostAlloc((void**)&chunk, 256 * sizeof(Status), cudaHostAllocDefault) != cudaSuccess) return false;
+            for (int i = 0; i < 256; ++i) free_.push_back(chunk + i);
+        }
+        return true;
+    }
     void release(Status* s) {
         if (!s) return;
         std::lock_guard<std::mutex> g(mu_);
@@ -93,6 +103,7 @@ struct OutState {
     int finalized = 0;
     int nonfinite = 0;          // fixed-point path met inf/nan: rerun in binary64
     int retry_sort = 0;         // bucket path gave up: rerun on the sort path
+    int borrowed_status = 0;    // status slot belongs to a cached batch graph
     int rc = TTV_OK;
 };
 
@@ -564,9 +575,277 @@ void ttv_out_free(ttv_out* out) {
     if (s->owned_subs) { cudaFreeAsync(s->owned_subs, s->stream); out->subs = nullptr; }
     if (s->owned_vals) { cudaFreeAsync(s->owned_vals, s->stream); out->vals = nullptr; }
     if (!s->finalized) cudaStreamSynchronize(s->stream);
-    g_status_pool.release(s->hstatus);
+    if (!s->borrowed_status) g_status_pool.release(s->hstatus);
     delete s;
     out->internal = nullptr;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched TTV: one CUDA graph per set of problems.
+namespace ttv {
+
+extern thread_local int t_capturing;      // ttv_prof.cu: no event records while capturing
+long long prof_add_launches(long long n);  // ttv_prof.cu
+
+struct BatchEntry {
+    uint64_t sig = 0;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<Status*> status;          // pinned, refreshed by every replay
+    std::vector<int> dense_out;
+    std::vector<ttv_out> shape;           // order, shape, is_dense, nnz of each result
+    long long launches = 0;               // kernel nodes per replay
+    void* arena = nullptr;                // library-owned workspace, if any
+    uint64_t last_use = 0;
+};
+
+static std::mutex g_batch_mu;
+static std::vector<BatchEntry*> g_batch_cache;
+static uint64_t g_batch_clock = 0;
+constexpr int kBatchStreams = 8;
+constexpr size_t kBatchCacheMax = 16;
+
+static uint64_t fnv(uint64_t h, const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+    return h;
+}
+template <typename T>
+static uint64_t fnv_v(uint64_t h, const T& v) { return fnv(h, &v, sizeof v); }
+
+static uint64_t batch_signature(const ttv_problem* probs, int32_t n, const ttv_out* outs, const ttv_opts* o) {
+    uint64_t h = 1469598103934665603ull;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    h = fnv_v(h, dev);
+    h = fnv_v(h, n);
+    h = fnv_v(h, o->fmt); h = fnv_v(h, o->path); h = fnv_v(h, o->accum); h = fnv_v(h, o->deterministic);
+    h = fnv_v(h, o->workspace); h = fnv_v(h, o->workspace_bytes);
+    for (int32_t i = 0; i < n; ++i) {
+        const ttv_tensor& t = probs[i].tensor;
+        h = fnv_v(h, t.subs); h = fnv_v(h, t.stride_nz); h = fnv_v(h, t.stride_mode); h = fnv_v(h, t.vals);
+        h = fnv_v(h, t.val_dtype); h = fnv_v(h, t.nnz); h = fnv_v(h, t.d);
+        if (t.shape) h = fnv(h, t.shape, sizeof(int64_t) * (size_t)std::max(0, std::min(t.d, TTV_MAX_D)));
+        h = fnv_v(h, probs[i].n_v); h = fnv_v(h, probs[i].v_dtype);
+        if (probs[i].modes) h = fnv(h, probs[i].modes, sizeof(int32_t) * (size_t)std::max(0, probs[i].n_v));
+        if (probs[i].vecs) h = fnv(h, probs[i].vecs, sizeof(void*) * (size_t)std::max(0, probs[i].n_v));
+        h = fnv_v(h, outs[i].subs); h = fnv_v(h, outs[i].vals);
+        h = fnv_v(h, outs[i].subs_capacity); h = fnv_v(h, outs[i].vals_capacity);
+    }
+    return h;
+}
+
+static cudaStream_t* side_streams() {
+    static cudaStream_t s[kBatchStreams + 1];
+    static std::once_flag f;
+    std::call_once(f, [] {
+        for (int i = 0; i <= kBatchStreams; ++i) cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking);
+    });
+    return s;
+}
+
+static void destroy_entry(BatchEntry* e) {
+    if (!e) return;
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    for (Status* s : e->status) g_status_pool.release(s);
+    if (e->arena) cudaFree(e->arena);
+    delete e;
+}
+
+static int batch_plans(const ttv_problem* probs, int32_t n, const ttv_opts* o, std::vector<Plan>& plans,
+                       std::vector<size_t>& ws_off, size_t& total) {
+    plans.resize((size_t)n);
+    ws_off.resize((size_t)n);
+    total = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const ttv_problem& q = probs[i];
+        int rc = make_plan(&q.tensor, q.modes, q.n_v, q.vecs, q.v_dtype, nullptr, o, plans[(size_t)i]);
+        if (rc != TTV_OK) return fail(rc, "problem %d: %s", i, g_err.c_str());
+        ws_off[(size_t)i] = total;
+        total += (workspace_bytes(plans[(size_t)i]) + 255) & ~size_t(255);
+    }
+    return TTV_OK;
+}
+
+static BatchEntry* batch_capture(const ttv_problem* probs, int32_t n, ttv_out* outs, const ttv_opts* o,
+                                 uint64_t sig, int& rc) {
+    std::vector<Plan> plans;
+    std::vector<size_t> ws_off;
+    size_t total = 0;
+    rc = batch_plans(probs, n, o, plans, ws_off, total);
+    if (rc != TTV_OK) return nullptr;
+    BatchEntry* e = new BatchEntry();
+    e->sig = sig;
+    char* ws = static_cast<char*>(o->workspace);
+    if (!ws || o->workspace_bytes < total) {
+        cudaError_t ce = cudaMalloc(&e->arena, std::max<size_t>(total, 256));
+        if (ce != cudaSuccess) { rc = cuda_fail(ce, "batch workspace"); delete e; return nullptr; }
+        ws = static_cast<char*>(e->arena);
+    }
+    // largest problems first, dealt round-robin over the streams
+    std::vector<int32_t> order((size_t)n);
+    for (int32_t i = 0; i < n; ++i) order[(size_t)i] = i;
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return probs[a].tensor.nnz > probs[b].tensor.nnz; });
+    cudaStream_t* ss = side_streams();
+    cudaStream_t cap = ss[kBatchStreams];
+    if (!g_status_pool.reserve((size_t)n + 8)) {
+        rc = fail(TTV_ERR_NOMEM, "pinned status allocation failed");
+        destroy_entry(e);
+        return nullptr;
+    }
+    cudaEvent_t fork, joins[kBatchStreams];
+    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int k = 0; k < kBatchStreams; ++k) cudaEventCreateWithFlags(&joins[k], cudaEventDisableTiming);
+    e->status.assign((size_t)n, nullptr);
+    e->dense_out.assign((size_t)n, 0);
+    e->shape.assign((size_t)n, ttv_out{});
+    t_capturing = 1;
+    const long long before = prof_add_launches(0);
+    cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) { t_capturing = 0; rc = cuda_fail(ce, "begin capture"); destroy_entry(e); return nullptr; }
+    cudaEventRecord(fork, cap);
+    const int nstreams = std::min<int>(kBatchStreams, std::max<int32_t>(1, n));
+    for (int k = 0; k < nstreams; ++k) cudaStreamWaitEvent(ss[k], fork, 0);
+    rc = TTV_OK;
+    for (size_t j = 0; j < order.size(); ++j) {
+        const int32_t i = order[j];
+        ttv_opts oi = *o;
+        oi.async = 1;
+        oi.workspace = ws + ws_off[(size_t)i];
+        oi.workspace_bytes = workspace_bytes(plans[(size_t)i]);
+        ttv_out tmp = outs[i];
+        tmp.internal = nullptr;
+        const int r = execute(plans[(size_t)i], &tmp, &oi, ss[j % nstreams]);
+        OutState* st = static_cast<OutState*>(tmp.internal);
+        if (st) {
+            e->status[(size_t)i] = st->hstatus;
+            e->dense_out[(size_t)i] = st->dense_out;
+            delete st;
+        }
+        tmp.internal = nullptr;
+        e->shape[(size_t)i] = tmp;
+        if (r != TTV_OK && rc == TTV_OK) rc = r;
+    }
+    for (int k = 0; k < nstreams; ++k) {
+        cudaEventRecord(joins[k], ss[k]);
+        cudaStreamWaitEvent(cap, joins[k], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    ce = cudaStreamEndCapture(cap, &graph);
+    t_capturing = 0;
+    e->launches = prof_add_launches(0) - before;
+    prof_add_launches(-e->launches);            // captured, not yet run
+    cudaEventDestroy(fork);
+    for (int k = 0; k < kBatchStreams; ++k) cudaEventDestroy(joins[k]);
+    if (ce != cudaSuccess || rc != TTV_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        if (rc == TTV_OK) rc = cuda_fail(ce, "end capture");
+        destroy_entry(e);
+        return nullptr;
+    }
+    ce = cudaGraphInstantiate(&e->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) { rc = cuda_fail(ce, "graph instantiate"); destroy_entry(e); return nullptr; }
+    return e;
+}
+
+}  // namespace ttv
+
+extern "C" {
+
+int ttv_batch_workspace_size(const ttv_problem* probs, int32_t n, const ttv_opts* opts, size_t* bytes) {
+    g_err.clear();
+    if (!probs || n < 0 || !bytes) return fail(TTV_ERR_ARG, "bad batch arguments");
+    ttv_opts def;
+    ttv_opts_init(&def);
+    const ttv_opts* o = opts ? opts : &def;
+    std::vector<Plan> plans;
+    std::vector<size_t> off;
+    size_t total = 0;
+    int rc = batch_plans(probs, n, o, plans, off, total);
+    if (rc != TTV_OK) return rc;
+    *bytes = total;
+    return TTV_OK;
+}
+
+long long ttv_batch_graph_launches(const ttv_problem* probs, int32_t n, const ttv_out* outs, const ttv_opts* opts) {
+    if (!probs || !outs || n <= 0) return 0;
+    ttv_opts def;
+    ttv_opts_init(&def);
+    const ttv_opts* o = opts ? opts : &def;
+    const uint64_t sig = batch_signature(probs, n, outs, o);
+    std::lock_guard<std::mutex> g(g_batch_mu);
+    for (BatchEntry* e : g_batch_cache)
+        if (e->sig == sig) return e->launches;
+    return 0;
+}
+
+void ttv_batch_release(void) {
+    std::lock_guard<std::mutex> g(g_batch_mu);
+    cudaDeviceSynchronize();
+    for (BatchEntry* e : g_batch_cache) destroy_entry(e);
+    g_batch_cache.clear();
+}
+
+int ttv_batch(const ttv_problem* probs, int32_t n, ttv_out* outs, const ttv_opts* opts, ttv_stream_t stream_) {
+    g_err.clear();
+    if (!probs || !outs || n < 0) return fail(TTV_ERR_ARG, "bad batch arguments");
+    if (n == 0) return TTV_OK;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!outs[i].vals) return fail(TTV_ERR_ARG, "batch results need caller buffers (problem %d)", i);
+        if (outs[i].internal) return fail(TTV_ERR_ARG, "ttv_out %d reused without ttv_out_free", i);
+    }
+    ttv_opts def;
+    ttv_opts_init(&def);
+    const ttv_opts* o = opts ? opts : &def;
+    init_once();
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    const uint64_t sig = batch_signature(probs, n, outs, o);
+    std::lock_guard<std::mutex> g(g_batch_mu);
+    BatchEntry* e = nullptr;
+    for (BatchEntry* c : g_batch_cache)
+        if (c->sig == sig) { e = c; break; }
+    if (!e) {
+        int rc = TTV_OK;
+        e = batch_capture(probs, n, outs, o, sig, rc);
+        if (!e) return rc;
+        if (g_batch_cache.size() >= kBatchCacheMax) {
+            auto it = std::min_element(g_batch_cache.begin(), g_batch_cache.end(),
+                                       [](BatchEntry* a, BatchEntry* b) { return a->last_use < b->last_use; });
+            cudaDeviceSynchronize();
+            destroy_entry(*it);
+            g_batch_cache.erase(it);
+        }
+        g_batch_cache.push_back(e);
+    }
+    e->last_use = ++g_batch_clock;
+    for (Status* s : e->status) memset(s, 0, sizeof(Status));
+    cudaError_t ce = cudaGraphLaunch(e->exec, stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph launch");
+    prof_add_launches(e->launches);
+    int first = TTV_OK;
+    for (int32_t i = 0; i < n; ++i) {
+        OutState* st = new OutState();
+        st->hstatus = e->status[(size_t)i];
+        st->borrowed_status = 1;
+        st->stream = stream;
+        st->dense_out = e->dense_out[(size_t)i];
+        outs[i].internal = st;
+        // shape and order are fixed by the problem
+        const ttv_out& sh = e->shape[(size_t)i];
+        outs[i].order = sh.order;
+        for (int j = 0; j < TTV_MAX_D; ++j) outs[i].shape[j] = sh.shape[j];
+        outs[i].dtype = TTV_F64;
+        outs[i].is_dense = sh.is_dense;
+        outs[i].nnz = sh.nnz;
+    }
+    if (o->async) return TTV_OK;
+    for (int32_t i = 0; i < n; ++i) {
+        const int r = finalize(&outs[i]);
+        if (r != TTV_OK && first == TTV_OK) first = r;
+    }
+    return first;
 }
 
 }  // extern "C"

@@ -24,6 +24,9 @@ static std::vector<Pending> g_pending;
 static std::vector<cudaEvent_t> g_free_events;
 static std::map<std::string, std::pair<double, long long>> g_totals;
 static thread_local Pending t_open{nullptr, nullptr, nullptr};
+thread_local int t_capturing = 0;     // inside a graph capture: count, never record events
+
+long long prof_add_launches(long long n) { return g_launches.fetch_add(n) + n; }
 
 static cudaEvent_t get_event() {
     if (!g_free_events.empty()) {
@@ -38,7 +41,7 @@ static cudaEvent_t get_event() {
 
 void prof_begin(const char* name, cudaStream_t s) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    if (t_capturing || !g_prof_on.load(std::memory_order_relaxed)) return;
     std::lock_guard<std::mutex> g(g_prof_mu);
     t_open.name = name;
     t_open.a = get_event();

@@ -1,0 +1,111 @@
+"""The continuous-batching server: every result in the mix equals the result
+of the same TTV run alone (ttv_multi), within the FP64 tolerance; budget
+admission and refusal; bounded waits."""
+import threading
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from parity import RTOL, FLOOR, check_result, oracle_ttv
+
+pytestmark = pytest.mark.gpu
+
+
+def _close(a, b, A):
+    a = a.cpu().numpy().reshape(-1)
+    b = b.cpu().numpy().reshape(-1)
+    A = A.cpu().numpy().reshape(-1)
+    assert a.shape == b.shape
+    assert np.all(np.abs(a - b) <= RTOL * np.maximum(np.abs(b), FLOOR * A))
+
+
+def test_server_mix_equals_alone(cuda_lib):
+    dev = "cuda"
+    g = np.random.default_rng(1)
+    tensors = []
+    for i, (shape, nnz) in enumerate([((300, 200, 100, 50), 200_000), ((50, 60, 70, 80), 50_000),
+                                      ((1000, 900, 800, 700), 400_000), ((20, 30, 40, 50), 20_000)]):
+        t = S.sptenrand(500 + i, shape, nnz, vals="u11")
+        tensors.append((t.subs.to(dev), t.vals.to(dev), shape))
+    srv = cuda_lib.Server(budget_bytes=8 << 30, slots=4)
+    ids = [srv.register(s, v, sh) for s, v, sh in tensors]
+    reqs = []
+    for j in range(48):
+        ti = int(g.integers(0, len(tensors)))
+        shape = tensors[ti][2]
+        nv = 1 + j % 2
+        modes = [int(m) for m in g.permutation(4)[:nv]]
+        vecs = [g.uniform(-1, 1, shape[m]) for m in modes]
+        reqs.append((ti, modes, vecs))
+    rids = [None] * len(reqs)
+
+    def client(lo, hi):
+        for k in range(lo, hi):
+            ti, modes, vecs = reqs[k]
+            rids[k] = srv.submit(ids[ti], modes, vecs)
+
+    th = [threading.Thread(target=client, args=(a, a + 12)) for a in range(0, 48, 12)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    results = [srv.wait(r, timeout_us=60_000_000) for r in rids]
+    for (ti, modes, vecs), res in zip(reqs, results):
+        subs, vals, shape = tensors[ti]
+        dv = [torch.from_numpy(v).to(dev) for v in vecs]
+        alone = cuda_lib.ttv_multi(subs, vals, shape, modes, dv)
+        A = cuda_lib.ttv_multi(subs, vals.abs(), shape, modes, [v.abs() for v in dv])
+        assert res.shape == alone.shape
+        assert torch.equal(res.subs, alone.subs)
+        _close(res.vals, alone.vals, A.vals)
+    # one against the oracle as well
+    ti, modes, vecs = reqs[0]
+    subs, vals, shape = tensors[ti]
+    ref, A = oracle_ttv(subs, vals, shape, modes, vecs)
+    check_result(results[0], ref, A)
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["pending"] == 0
+    assert 0 < st["p50_us"] <= st["p99_us"] <= st["max_us"]
+    srv.close()
+
+
+def test_server_float32_storage(cuda_lib):
+    dev = "cuda"
+    t = S.sptenrand(77, (200, 300, 400, 50), 150_000, vals="u11")
+    subs, vals32 = t.subs.to(dev), t.vals.to(torch.float32).to(dev)
+    srv = cuda_lib.Server(budget_bytes=4 << 30, slots=2)
+    tid = srv.register(subs, vals32, t.shape)
+    x = np.random.default_rng(3).uniform(-1, 1, 300).astype(np.float32)
+    res = srv.wait(srv.submit(tid, [1], [x], accum="compensated"))
+    ref, A = oracle_ttv(subs, vals32, t.shape, [1], [x])
+    check_result(res, ref, A)
+    srv.close()
+
+
+def test_server_budget_and_timeout(cuda_lib):
+    dev = "cuda"
+    t = S.sptenrand(78, (100, 100, 100), 100_000, vals="u11")
+    subs, vals = t.subs.to(dev), t.vals.to(dev)
+    tiny = cuda_lib.Server(budget_bytes=1 << 20, slots=1)
+    with pytest.raises(cuda_lib.TTVError) as e:
+        tiny.register(subs, vals, t.shape)
+    assert e.value.name == "TTV_ERR_BUDGET"
+    tiny.close()
+    # room for the tensor but not for a request's sort workspace
+    srv = cuda_lib.Server(budget_bytes=int(100_000 * 32 * 1.05), slots=1)
+    tid = srv.register(subs, vals, t.shape)
+    with pytest.raises(cuda_lib.TTVError) as e:
+        srv.submit(tid, [0], [np.ones(100)], path="sort")
+    assert e.value.name == "TTV_ERR_BUDGET"
+    srv.close()
+    srv = cuda_lib.Server(budget_bytes=2 << 30, slots=1)
+    tid = srv.register(subs, vals, t.shape)
+    rid = srv.submit(tid, [0], [np.ones(100)])
+    r = srv.wait(rid, timeout_us=30_000_000)
+    assert r.vals.numel() > 0
+    with pytest.raises(cuda_lib.TTVError) as e:
+        srv.wait(123456, timeout_us=1000)
+    assert e.value.name == "TTV_ERR_TIMEOUT"
+    srv.close()
