@@ -42,6 +42,10 @@ WORKLOADS = {
     "single_5way_zipf": dict(
         make=lambda dev, seed, nnz=None: S.single_5way_zipf(seed=seed, device=dev, nnz=nnz or 100_000_000), fmt="sparse",
         desc="single TTV mode 2 of a 20000x5000x100000x2000x500 COO tensor, nnz 1e8 Zipf(1.2) distinct, N(0,1), sparse 4-way result"),
+    "batch_512": dict(make=None, fmt="sparse",
+        desc="512 independent 3-to-5-way COO tensors, nnz log-uniform [1e3, 2e6], sizes U[50, 50000], own mode each, one graph launch"),
+    "serve_64": dict(make=None, fmt="sparse",
+        desc="Poisson TTV requests against 64 resident 4-way FP32 tensors (nnz log-uniform [1e4, 5e7]), random mode, fresh vectors"),
     "single_3way_100": dict(
         make=lambda dev, seed, nnz=None: S.single_3way_100(seed=seed, device=dev), fmt="sparse",
         desc="single TTV mode 0 of a 100^3 COO tensor, nnz 1e4 uniform distinct, sparse 100x100 result"),
@@ -211,15 +215,23 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--scale", type=float, default=1.0, help="nnz scale for batch_512 / serve_64")
+    ap.add_argument("--requests", type=int, default=2000, help="serve_64: requests in the timed stream")
+    ap.add_argument("--rate", type=float, default=20000.0, help="serve_64: Poisson arrival rate (req/s)")
     args = ap.parse_args()
     if args.seed == 0:
-        args.seed = {"allbutone_4way_1000": 2, "single_5way_zipf": 3, "single_3way_100": 1}[args.workload]
+        args.seed = {"allbutone_4way_1000": 2, "single_5way_zipf": 3, "single_3way_100": 1, "batch_512": 5,
+                     "serve_64": 6}[args.workload]
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch_512":
+        return run_batch(args, rank, world, local_rank)
+    if args.workload == "serve_64":
+        return run_serve(args, rank, world, local_rank)
 
     import paper_2510_01495_gb300 as ttv
     torch.cuda.set_device(local_rank)
@@ -374,6 +386,164 @@ def main():
                                 "sample": f"first {m} of {nnz} nonzeros, one call, {dt:.1f} s"}
     if dist:
         dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _clock_start(local_rank):
+    c = ClockSampler(local_rank)
+    c.start()
+    time.sleep(0.3)
+    return c
+
+
+def run_batch(args, rank, world, local_rank):
+    """512 independent TTVs per step: one graph launch (ttv_batch) against a
+    loop of single asynchronous ttv_multi launches over the same problems."""
+    import paper_2510_01495_gb300 as ttv
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    ttv.load()
+    probs = S.batch_problems(seed=args.seed + 1000 * rank, count=512, scale=args.scale, device=dev)
+    items = []
+    for p in probs:
+        t = p.tensor
+        items.append((t.subs.t().contiguous().t(), t.vals, t.shape, p.modes, p.vecs))
+    total_nnz = sum(p.tensor.nnz for p in probs)
+    b = ttv.Batch(items)
+    for _ in range(args.warmup):
+        b.run()
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    clocks = _clock_start(local_rank)
+    ttv.profile_reset()
+    ttv.profile_enable(False)
+    l0 = ttv.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        b.run()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = ttv.launch_count() - l0
+    clk = clocks.stop()
+    # the plain form: one launch sequence per problem, same buffers
+    outs = [(ttv.workspace_size(it[0], it[1], it[2], it[3]), ttv.out_capacity(it[0], it[1], it[2], it[3]))
+            for it in items]
+    wss = [torch.empty(max(1, w), dtype=torch.uint8, device=dev) for w, _ in outs]
+    ovs = [torch.empty(max(1, c[1]), dtype=torch.float64, device=dev) for _, c in outs]
+    oss = [torch.empty((max(1, c[0]), len(it[2]) - len(it[3])), dtype=torch.int64, device=dev)
+           for (_, c), it in zip(outs, items)]
+
+    def loop_once():
+        for it, w, ov, os_ in zip(items, wss, ovs, oss):
+            ttv.ttv_multi(it[0], it[1], it[2], it[3], it[4], workspace=w, out_vals=ov, out_subs=os_)
+
+    for _ in range(max(1, args.warmup // 2)):
+        loop_once()
+    torch.cuda.synchronize(dev)
+    k2 = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(k2):
+        loop_once()
+    torch.cuda.synchronize(dev)
+    ms_loop = (time.perf_counter() - t0) * 1e3 / k2
+    value = total_nnz * world / (ms * 1e-3) / 1e9
+    line = {
+        "metric": "TTV nonzeros/sec", "value": value, "unit": "GNNZ/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batch_512", "desc": WORKLOADS["batch_512"]["desc"], "problems": len(probs),
+                   "nnz_total": total_nnz, "scale": args.scale, "l2": "inputs larger than L2 (no flush)"},
+        "loop_of_singles": {"value": total_nnz / (ms_loop * 1e-3) / 1e9, "unit": "GNNZ/s", "ms_per_step": ms_loop,
+                            "note": "one synchronous ttv_multi per problem (host-timed)"},
+        "graph_kernel_launches_per_step": b.graph_launches(), "gpu_launches": launches, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args, rank, world, local_rank):
+    """Poisson stream of TTV requests against resident FP32 tensors through
+    the continuous-batching server (8 slots), against the plain
+    one-request-at-a-time form (1 slot, submit then wait); p50/p99 latency
+    beside throughput."""
+    import paper_2510_01495_gb300 as ttv
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    ttv.load()
+    g = np.random.default_rng(args.seed + rank)
+    tensors = []
+    for i in range(64):
+        s = args.seed * 1000 + i
+        r = S.uniform(s, 9, 2).numpy()
+        nnz = max(1000, int(math.exp(math.log(1e4) + r[0] * (math.log(5e7) - math.log(1e4))) * args.scale))
+        shp = None
+        for tries in range(100):
+            shp = tuple(int(x) for x in (S.uniform_int(s, 11 + tries, 4, 4901).numpy() + 100))
+            if nnz <= 0.01 * float(np.prod([float(x) for x in shp])):
+                break
+        t = S.sptenrand(s, shp, nnz, vals="u11", device=dev)
+        tensors.append((t.subs, t.vals.to(torch.float32), shp, nnz))
+    resident = sum(x[3] * (4 * 8 + 4) for x in tensors)
+    srv = ttv.Server(budget_bytes=60 << 30, slots=8)
+    plain = ttv.Server(budget_bytes=60 << 30, slots=1)
+    ids = [srv.register(sb, vl, sh) for sb, vl, sh, _ in tensors]
+    pids = [plain.register(sb, vl, sh) for sb, vl, sh, _ in tensors]
+    nnzs = [x[3] for x in tensors]
+    shapes = [x[2] for x in tensors]
+    del tensors
+    torch.cuda.empty_cache()
+    reqs = []
+    for _ in range(args.requests + 64):
+        ti = int(g.integers(0, len(ids)))
+        m = int(g.integers(0, 4))
+        reqs.append((ti, m, g.uniform(-1, 1, shapes[ti][m]).astype(np.float32)))
+    for ti, m, x in reqs[:64]:
+        srv.wait(srv.submit(ids[ti], [m], [x], accum="compensated"))
+        plain.wait(plain.submit(pids[ti], [m], [x], accum="compensated"))
+    srv.reset_stats()
+    clocks = _clock_start(local_rank)
+    arrivals = np.cumsum(g.exponential(1.0 / args.rate, size=args.requests))
+    rids = []
+    t0 = time.perf_counter()
+    for k, (ti, m, x) in enumerate(reqs[64:]):
+        delay = arrivals[k] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        rids.append(srv.submit(ids[ti], [m], [x], accum="compensated"))
+    for r in rids:
+        srv.wait(r)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    clk = clocks.stop()
+    served_nnz = sum(nnzs[ti] for ti, _, _ in reqs[64:])
+    n_plain = min(300, args.requests)
+    plain.reset_stats()
+    t1 = time.perf_counter()
+    for ti, m, x in reqs[64:64 + n_plain]:
+        plain.wait(plain.submit(pids[ti], [m], [x], accum="compensated"))
+    wall_plain = time.perf_counter() - t1
+    pst = plain.stats()
+    plain_nnz = sum(nnzs[ti] for ti, _, _ in reqs[64:64 + n_plain])
+    srv.close()
+    plain.close()
+    line = {
+        "metric": "TTV nonzeros/sec", "value": served_nnz / wall / 1e9, "unit": "GNNZ/s", "n_gpus": world,
+        "steps": args.requests, "warmup": 64, "ms_per_step": 1e3 * wall / args.requests, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 storage, f64 compensated accumulation",
+        "data": "synthetic",
+        "config": {"workload": "serve_64", "desc": WORKLOADS["serve_64"]["desc"], "rate_req_s": args.rate,
+                   "requests": args.requests, "scale": args.scale, "resident_bytes": resident, "slots": 8,
+                   "budget_bytes": 60 << 30},
+        "serve": {"p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
+                  "throughput_rps": args.requests / wall, "completed": st["completed"]},
+        "plain": {"requests": n_plain, "throughput_rps": n_plain / wall_plain,
+                  "throughput_gnnz_s": plain_nnz / wall_plain / 1e9, "p50_ms": pst["p50_us"] / 1e3,
+                  "p99_ms": pst["p99_us"] / 1e3},
+        "clocks": clk,
+    }
     if rank == 0:
         print(json.dumps(line), flush=True)
 

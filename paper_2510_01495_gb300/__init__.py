@@ -509,6 +509,9 @@ def _take_result(lib, out: Out) -> Result:
             subs = torch.zeros((n, out.order), dtype=torch.int64, device=dev)
         return Result(subs, vals, newshape, False)
     finally:
+        # the copies above run on torch's stream; the result's memory returns to
+        # the library's stream-ordered pool only after they have finished
+        torch.cuda.current_stream().synchronize()
         lib.ttv_out_free(ctypes.byref(out))
 
 

@@ -109,6 +109,7 @@ void complete(ttv_server* s, Slot& sl) {
     std::shared_ptr<Request> r = sl.req;
     sl.req.reset();
     if (r->rc == TTV_OK) r->rc = ttv_out_sync(&r->out);
+    // the result now belongs to the client: its buffers must not be touched here
     if (r->dvecs) cudaFreeAsync(r->dvecs, sl.stream);
     r->latency_us = std::chrono::duration<double, std::micro>(Clock::now() - r->submitted).count();
     std::lock_guard<std::mutex> g(s->mu);
@@ -181,9 +182,14 @@ void start(ttv_server* s, Slot& sl, const std::shared_ptr<Request>& r) {
 void scheduler(ttv_server* s) {
     cudaSetDevice(s->device);
     for (;;) {
-        // completions
-        for (Slot& sl : s->slots)
-            if (sl.req && cudaEventQuery(sl.done) == cudaSuccess) complete(s, sl);
+        // completions (an error state also ends the request: it is reported, never waited on)
+        for (Slot& sl : s->slots) {
+            if (!sl.req) continue;
+            const cudaError_t q = cudaEventQuery(sl.done);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess && sl.req->rc == TTV_OK) sl.req->rc = ttv::cuda_fail(q, "request");
+            complete(s, sl);
+        }
         std::unique_lock<std::mutex> lk(s->mu);
         if (s->stop && s->queue.empty()) {
             bool busy = false;
