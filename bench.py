@@ -220,6 +220,7 @@ def main():
     ap.add_argument("--layout", default="soa", choices=["soa", "aos"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--nnz", type=int, default=None, help="smaller case of the workload (profiling)")
+    ap.add_argument("--no-tune", action="store_true", help="batch_512: skip the autotuner (planner rule only)")
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -419,6 +420,22 @@ def run_batch(args, rank, world, local_rank):
         t = p.tensor
         items.append((t.subs.t().contiguous().t(), t.vals, t.shape, p.modes, p.vecs))
     total_nnz = sum(p.tensor.nnz for p in probs)
+    # autotune: one record per problem class (untimed), consulted when the
+    # graph is captured and by the loop of singles alike
+    t_tune = time.perf_counter()
+    tuned = 0
+    if not args.no_tune:
+        ttv.tune_clear()
+        for it in items:
+            if ttv.tune_lookup(it[0], it[1], it[2], it[3]) is None:
+                ttv.autotune(it[0], it[1], it[2], it[3], it[4], trials=2)
+                tuned += 1
+    t_tune = time.perf_counter() - t_tune
+    chosen = {}
+    for it in items:
+        rec = ttv.tune_lookup(it[0], it[1], it[2], it[3])
+        key = rec[0] if rec else "untuned"
+        chosen[key] = chosen.get(key, 0) + 1
     b = ttv.Batch(items)
     for _ in range(args.warmup):
         b.run()
@@ -468,6 +485,7 @@ def run_batch(args, rank, world, local_rank):
         "loop_of_singles": {"value": total_nnz / (ms_loop * 1e-3) / 1e9, "unit": "GNNZ/s", "ms_per_step": ms_loop,
                             "note": "one synchronous ttv_multi per problem (host-timed)"},
         "graph_kernel_launches_per_step": b.graph_launches(), "gpu_launches": launches, "clocks": clk,
+        "autotune": {"classes_tuned": tuned, "seconds": round(t_tune, 2), "problems_by_path": chosen},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

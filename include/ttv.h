@@ -70,10 +70,12 @@ typedef enum {
 } ttv_out_format;
 
 typedef enum {
-    TTV_PATH_AUTO = 0,           /* planner / autotuner choice                        */
+    TTV_PATH_AUTO = 0,           /* autotuner record, else the planner's rule         */
     TTV_PATH_DENSE = 1,          /* block-private dense accumulator (small prod R)    */
     TTV_PATH_SORT = 2,           /* LSD onesweep radix sort + segmented reduction     */
-    TTV_PATH_HASH = 3,           /* warp-aggregated HBM hash table + compaction       */
+    TTV_PATH_HASH = 3,           /* warp-combined table in HBM (direct-indexed or open
+                                    addressing) + compaction; not deterministic, so
+                                    deterministic/compensated calls use SORT         */
     TTV_PATH_BUCKET = 4          /* splitter partition + in-shared-memory sort        */
 } ttv_path;
 
@@ -204,6 +206,50 @@ int ttv_batch_workspace_size(const ttv_problem *probs, int32_t n, const ttv_opts
  * it is not cached). */
 long long ttv_batch_graph_launches(const ttv_problem *probs, int32_t n, const ttv_out *outs, const ttv_opts *opts);
 void ttv_batch_release(void);
+
+/* ---- autotuner ----------------------------------------------------------------
+ * The paper has no counterpart: it times one fixed CPU kernel per language.
+ * Problems fall into classes by (order d, surviving modes, result format,
+ * value and vector dtypes, subscript layout, ceil(log2 nnz), ceil(log2 of
+ * the key space prod shape[R])).  ttv_autotune runs every applicable
+ * candidate on the given problem -- accumulation path (DENSE, SORT, HASH,
+ * BUCKET) x CTAs per SM of the streaming pass (1-4 for DENSE, 4/8/16 for SORT
+ * and HASH) -- `trials` times after one warm-up run each, takes the median
+ * of CUDA-event times on `stream`, and records the fastest for the class.
+ * Every later call with path AUTO, fp64 accumulation and no determinism
+ * request (ttv_multi, ttv_batch, the server) whose problem falls in a
+ * recorded class uses the recorded plan; other calls are unaffected.  The
+ * record lives in host memory, shared by all threads; ttv_tune_save /
+ * ttv_tune_load keep it in a text file ("ttv-tune 1" header, then one
+ * "<class hex> <path> <ctas_per_sm> <ms>" line per class; loading merges).
+ * ttv_autotune synchronises `stream` once per trial and allocates its own
+ * workspace and results; it returns TTV_ERR_ARG for deterministic or
+ * non-fp64 options and TTV_ERR_UNSUPPORTED when no candidate can run (an
+ * empty tensor). */
+#define TTV_TUNE_MAX_CANDIDATES 16
+typedef struct {
+    int32_t path;                /* chosen ttv_path                                */
+    int32_t ctas_per_sm;         /* chosen CTAs per SM of the streaming pass        */
+    double ms;                   /* its median time                                */
+    int32_t n_candidates;        /* candidates that ran                             */
+    int32_t cand_path[TTV_TUNE_MAX_CANDIDATES];
+    int32_t cand_ctas[TTV_TUNE_MAX_CANDIDATES];
+    double cand_ms[TTV_TUNE_MAX_CANDIDATES];
+} ttv_tune_result;
+
+int ttv_autotune(const ttv_tensor *t, const int32_t *modes, int32_t n_v, const void *const *vecs,
+                 ttv_dtype v_dtype, const ttv_opts *opts, int32_t trials, ttv_tune_result *result,
+                 ttv_stream_t stream);
+int ttv_tune_save(const char *path);     /* TTV_ERR_ARG if the file can not be written */
+int ttv_tune_load(const char *path);     /* TTV_ERR_ARG on a missing or malformed file;
+                                            nothing is merged then                     */
+void ttv_tune_clear(void);
+int ttv_tune_count(void);                /* recorded classes */
+/* 1 and the recorded plan if the problem's class (vectors taken as FP64 for
+ * the class key) has a record, 0 if not, a negative error code for an
+ * invalid problem.  path / ctas_per_sm may be NULL. */
+int ttv_tune_lookup(const ttv_tensor *t, const int32_t *modes, int32_t n_v, const ttv_opts *opts, int32_t *path,
+                    int32_t *ctas_per_sm);
 
 /* ---- serving ------------------------------------------------------------------
  * A continuous-batching TTV server.  Registered tensors stay resident in

@@ -312,6 +312,88 @@ def profile_names():
     return [x for x in buf.value.decode().split("\n") if x]
 
 
+# ---- autotuner ------------------------------------------------------------------
+
+TUNE_MAX = 16
+PATH_NAME = {v: k for k, v in PATH.items()}
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("ms", ctypes.c_double),
+                ("n_candidates", ctypes.c_int32), ("cand_path", ctypes.c_int32 * TUNE_MAX),
+                ("cand_ctas", ctypes.c_int32 * TUNE_MAX), ("cand_ms", ctypes.c_double * TUNE_MAX)]
+
+
+def _declare_tune(lib):
+    if getattr(lib, "_tune_declared", False):
+        return lib
+    P = ctypes.POINTER
+    lib.ttv_autotune.argtypes = [P(Tensor), P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_void_p), ctypes.c_int,
+                                 P(Opts), ctypes.c_int32, P(TuneResult), ctypes.c_void_p]
+    lib.ttv_autotune.restype = ctypes.c_int
+    lib.ttv_tune_save.argtypes = [ctypes.c_char_p]
+    lib.ttv_tune_save.restype = ctypes.c_int
+    lib.ttv_tune_load.argtypes = [ctypes.c_char_p]
+    lib.ttv_tune_load.restype = ctypes.c_int
+    lib.ttv_tune_clear.argtypes = []
+    lib.ttv_tune_clear.restype = None
+    lib.ttv_tune_count.argtypes = []
+    lib.ttv_tune_count.restype = ctypes.c_int
+    lib.ttv_tune_lookup.argtypes = [P(Tensor), P(ctypes.c_int32), ctypes.c_int32, P(Opts), P(ctypes.c_int32),
+                                    P(ctypes.c_int32)]
+    lib.ttv_tune_lookup.restype = ctypes.c_int
+    lib._tune_declared = True
+    return lib
+
+
+def autotune(subs, vals, shape, modes, vecs, *, fmt="sparse", trials=5, deterministic=False, stream=None) -> dict:
+    """Times every applicable (path, CTAs per SM) plan on this problem and
+    records the fastest for its problem class (see ttv_autotune)."""
+    lib = _declare_tune(load())
+    vdt = vecs[0].dtype
+    t = make_tensor(subs, vals, shape)
+    m = (ctypes.c_int32 * len(modes))(*[int(x) for x in modes])
+    vp = (ctypes.c_void_p * len(vecs))(*[v.data_ptr() for v in vecs])
+    o = make_opts(fmt=fmt, deterministic=deterministic)
+    r = TuneResult()
+    _check(lib, lib.ttv_autotune(ctypes.byref(t), m, len(modes), vp, DTYPE[vdt], ctypes.byref(o), int(trials),
+                                 ctypes.byref(r), _stream_handle(stream)))
+    cands = [{"path": PATH_NAME[r.cand_path[i]], "ctas_per_sm": r.cand_ctas[i], "ms": r.cand_ms[i]}
+             for i in range(r.n_candidates)]
+    return {"path": PATH_NAME[r.path], "ctas_per_sm": r.ctas_per_sm, "ms": r.ms, "candidates": cands}
+
+
+def tune_lookup(subs, vals, shape, modes, *, fmt="sparse"):
+    """(path name, CTAs per SM) recorded for this problem's class, or None."""
+    lib = _declare_tune(load())
+    t = make_tensor(subs, vals, shape)
+    m = (ctypes.c_int32 * len(modes))(*[int(x) for x in modes])
+    o = make_opts(fmt=fmt)
+    pth, ctas = ctypes.c_int32(), ctypes.c_int32()
+    rc = lib.ttv_tune_lookup(ctypes.byref(t), m, len(modes), ctypes.byref(o), ctypes.byref(pth), ctypes.byref(ctas))
+    if rc < 0:
+        _check(lib, rc)
+    return (PATH_NAME[pth.value], ctas.value) if rc == 1 else None
+
+
+def tune_save(path: str):
+    lib = _declare_tune(load())
+    _check(lib, lib.ttv_tune_save(os.fsencode(path)))
+
+
+def tune_load(path: str):
+    lib = _declare_tune(load())
+    _check(lib, lib.ttv_tune_load(os.fsencode(path)))
+
+
+def tune_clear():
+    _declare_tune(load()).ttv_tune_clear()
+
+
+def tune_count() -> int:
+    return int(_declare_tune(load()).ttv_tune_count())
+
+
 # ---- allocation-free dense TTV -----------------------------------------------
 
 def ttv_dense_noalloc(subs: torch.Tensor, vals: torch.Tensor, shape, modes, vecs, out: torch.Tensor,

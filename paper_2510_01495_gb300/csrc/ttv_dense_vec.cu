@@ -196,7 +196,7 @@ int dense_vec_grid(const StreamDesc& p, int want_presence) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kVecThreads, smem);
-    per_sm = std::max(1, std::min(per_sm, 4));
+    per_sm = std::max(1, std::min(per_sm, p.ctas_per_sm > 0 ? p.ctas_per_sm : 4));
     const int64_t min_chunk = std::max<int64_t>((int64_t)kVecThreads * kVecPairs * 2 * 4, (int64_t)p.nkeys * 4);
     const int64_t by_work = std::max<int64_t>(1, (p.nnz + min_chunk - 1) / min_chunk);
     return (int)std::max<int64_t>(1, std::min<int64_t>(by_work, (int64_t)num_sms() * per_sm));

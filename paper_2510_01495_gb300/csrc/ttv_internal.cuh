@@ -56,6 +56,7 @@ struct StreamDesc {
     int64_t rshape[kMaxD];            // shape of the result
     uint64_t rmagic[kMaxD];           // division by rshape[j] (see udiv_invariant)
     uint32_t rsh[kMaxD];              // shift pair: sh1 | sh2 << 8
+    int32_t ctas_per_sm;              // grid of the streaming pass: CTAs per SM (0: default)
     Status* status;
 };
 
@@ -335,7 +336,10 @@ struct SortBuffers {
 
 size_t sort_workspace_bytes(int64_t n, int bits);
 // Sorts (keys, vals) stably by the low `bits` bits of the key; returns which
-// buffer (0/1) holds the result.
-int radix_sort_pairs(SortBuffers& sb, int64_t n, int bits, Status* st, cudaStream_t stream);
+// buffer (0/1) holds the result.  With n_dev, the pair count is
+// min(n, *n_dev), read on the device (n is then the upper bound the buffers
+// and grids are sized for).
+int radix_sort_pairs(SortBuffers& sb, int64_t n, int bits, Status* st, cudaStream_t stream,
+                     const unsigned long long* n_dev = nullptr);
 
 }  // namespace ttv

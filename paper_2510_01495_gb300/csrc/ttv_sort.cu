@@ -79,8 +79,10 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_
 // ---------------------------------------------------------------------------
 // Histogram of every digit pass in one read of the keys.
 __global__ void __launch_bounds__(256) k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int npass,
-                                                    uint32_t* __restrict__ hist) {
+                                                    uint32_t* __restrict__ hist,
+                                                    const unsigned long long* __restrict__ n_dev) {
     __shared__ uint32_t sh[8 * kRadix];
+    if (n_dev) n = min(n, (int64_t)*n_dev);
     for (int i = threadIdx.x; i < npass * kRadix; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -123,7 +125,8 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint64_t* __res
                                                            uint64_t* __restrict__ keys_out,
                                                            double* __restrict__ vals_out, int64_t n, int shift,
                                                            const uint32_t* __restrict__ digit_off,
-                                                           uint32_t* lookback, uint32_t* ticket, Status* st) {
+                                                           uint32_t* lookback, uint32_t* ticket, Status* st,
+                                                           const unsigned long long* __restrict__ n_dev) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OnesweepSmem& sm = *reinterpret_cast<OnesweepSmem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -133,6 +136,10 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint64_t* __res
     __syncthreads();
     const uint32_t tile = sm.tile;
     const int64_t base = (int64_t)tile * kSortTile;
+    // With the count on the device, tiles past it have nothing to do; no
+    // tile with work waits on them (look-back only reads earlier tiles).
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    if (base >= n) return;
 
     uint64_t k[kSortItems];
     double v[kSortItems];
@@ -238,7 +245,8 @@ size_t sort_workspace_bytes(int64_t n, int bits) {
     return b;
 }
 
-int radix_sort_pairs(SortBuffers& sb, int64_t n, int bits, Status* st, cudaStream_t stream) {
+int radix_sort_pairs(SortBuffers& sb, int64_t n, int bits, Status* st, cudaStream_t stream,
+                     const unsigned long long* n_dev) {
     const int npass = bits <= 0 ? 0 : (bits + kRadixBits - 1) / kRadixBits;
     if (npass == 0 || n <= 1) return 0;
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
@@ -249,7 +257,7 @@ int radix_sort_pairs(SortBuffers& sb, int64_t n, int bits, Status* st, cudaStrea
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int hblocks = (int)std::min<int64_t>((int64_t)nsm * 4, (n + 255) / 256);
-    TTV_LAUNCH("radix_hist", stream, k_radix_hist<<<hblocks, 256, 0, stream>>>(sb.keys[0], n, npass, sb.hist));
+    TTV_LAUNCH("radix_hist", stream, k_radix_hist<<<hblocks, 256, 0, stream>>>(sb.keys[0], n, npass, sb.hist, n_dev));
     TTV_LAUNCH("radix_hist_scan", stream, k_radix_hist_scan<<<1, 256, 0, stream>>>(sb.hist, npass));
     const size_t smem = sizeof(OnesweepSmem);
     static bool attr_set = false;
@@ -261,7 +269,7 @@ int radix_sort_pairs(SortBuffers& sb, int64_t n, int bits, Status* st, cudaStrea
     for (int p = 0; p < npass; ++p) {
         TTV_LAUNCH("onesweep", stream, k_onesweep<<<(unsigned)ntiles, kSortThreads, smem, stream>>>(
             sb.keys[cur], sb.vals[cur], sb.keys[cur ^ 1], sb.vals[cur ^ 1], n, p * kRadixBits,
-            sb.hist + p * kRadix, sb.lookback + (size_t)p * ntiles * kRadix, sb.tickets + p, st));
+            sb.hist + p * kRadix, sb.lookback + (size_t)p * ntiles * kRadix, sb.tickets + p, st, n_dev));
         cur ^= 1;
     }
     return cur;

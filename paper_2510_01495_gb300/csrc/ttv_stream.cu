@@ -56,7 +56,8 @@ void launch_keys_terms(const StreamDesc& p, uint64_t* keys, double* terms, cudaS
     const size_t smem = p.vec_smem ? (size_t)p.vtotal * sizeof(double) : 0;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_keys_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int64_t want = (p.nnz + kStreamThreads * kUnroll - 1) / (kStreamThreads * kUnroll);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 8));
+    const int per_sm = p.ctas_per_sm > 0 ? p.ctas_per_sm : 8;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * per_sm));
     TTV_LAUNCH("keys_terms", stream, k_keys_terms<<<grid, kStreamThreads, smem, stream>>>(p, keys, terms));
 }
 
@@ -250,7 +251,7 @@ int dense_grid(const StreamDesc& p, int want_presence) {
         cudaFuncSetAttribute(k_dense_accum<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_accum<false>, kStreamThreads, smem);
     }
-    per_sm = std::max(1, std::min(per_sm, 4));
+    per_sm = std::max(1, std::min(per_sm, p.ctas_per_sm > 0 ? p.ctas_per_sm : 4));
     // at least ~4 unrolled sweeps of the block per CTA so that zeroing and
     // writing the partial array stay small next to the streaming work
     const int64_t min_chunk = std::max<int64_t>((int64_t)kStreamThreads * kUnroll * 4, (int64_t)p.nkeys * 4);

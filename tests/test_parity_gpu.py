@@ -262,3 +262,82 @@ def test_bucket_near_heavy_keys_at_range_top(cuda_lib):
     p = S.Problem(S.SparseTensor(torch.from_numpy(subs), torch.from_numpy(vals), (5000, 30, 1000)), [1],
                   [torch.from_numpy(x)], name="bucket_near_heavy")
     run_case(cuda_lib, p, path="bucket", layout="soa")
+
+
+# ---- hash path (direct-indexed or open-addressing table in HBM) --------------------
+
+@pytest.mark.parametrize("layout", ["aos", "soa"])
+@pytest.mark.parametrize("case", [
+    # direct table: key space <= 4 x the table bound (no sort)
+    ((300, 300, 300), 100_003, [0], "sparse"),
+    ((300, 300, 300), 100_003, [0], "dense"),
+    ((60, 70, 80, 90), 250_001, [1, 3], "sparse"),
+    # hashed table: large key space, distinct keys sorted afterwards
+    ((200, 300, 400, 500), 200_001, [1], "sparse"),
+    ((100, 1000, 1000), 1_001, [0], "dense"),
+    ((5, 6, 7, 8, 9), 7_777, [4], "sparse"),
+    ((2000, 500, 10000, 200, 50), 50_000, [2], "sparse"),
+])
+def test_hash_path(cuda_lib, case, layout):
+    shape, nnz, modes, fmt = case
+    p = rand_problem(301 + nnz, shape, nnz, modes)
+    run_case(cuda_lib, p, path="hash", fmt=fmt, layout=layout)
+
+
+@pytest.mark.parametrize("shape", [(3, 50, 2), (3000, 50, 2000)])
+def test_hash_duplicates_and_heavy_keys(cuda_lib, shape):
+    # 5000 copies of one surviving tuple, duplicate input subscripts, keys that
+    # repeat inside a warp (warp-combined before the table)
+    g = np.random.default_rng(4)
+    n = 40_000
+    subs = np.stack([g.integers(0, 3, n), g.integers(0, 50, n), g.integers(0, 2, n)], axis=1)
+    subs[:5000, 0] = 1
+    subs[:5000, 2] = 1
+    subs[20_000:20_064] = subs[20_000]
+    vals = g.uniform(-1, 1, n)
+    x = g.uniform(-1, 1, 50)
+    p = S.Problem(S.SparseTensor(torch.from_numpy(subs), torch.from_numpy(vals), shape), [1],
+                  [torch.from_numpy(x)], name="hash_heavy")
+    run_case(cuda_lib, p, path="hash")
+    run_case(cuda_lib, p, path="hash", fmt="dense")
+
+
+def test_hash_zipf_reduced(cuda_lib):
+    shape = (2000, 500, 10000, 200, 50)
+    p = S.single_5way_zipf(nnz=400_000, shape=shape)
+    res = run_case(cuda_lib, p, path="hash", layout="soa")
+    assert res.vals.numel() > 100_000
+
+
+def test_hash_float32_and_order0(cuda_lib):
+    p = rand_problem(41, (600, 70, 800), 60_000, [1])
+    run_case(cuda_lib, p, path="hash", val_dtype=torch.float32, vec_dtype=torch.float32)
+    p = rand_problem(42, (9, 8, 7), 300, [0, 1, 2])
+    res = run_case(cuda_lib, p, path="hash")
+    assert res.vals.numel() == 1
+
+
+@pytest.mark.parametrize("shape", [(200, 300, 400, 500), (300, 300, 300)])   # hashed, direct
+def test_hash_capacity_and_subscript_errors(cuda_lib, shape):
+    p = rand_problem(43, shape, 20_000, [1])
+    subs, vals, vecs = to_device(p)
+    small_subs = torch.empty((10, len(shape) - 1), dtype=torch.int64, device="cuda")
+    small_vals = torch.empty(10, dtype=torch.float64, device="cuda")
+    with pytest.raises(cuda_lib.TTVError) as e:
+        cuda_lib.ttv_multi(subs, vals, p.tensor.shape, p.modes, vecs, path="hash",
+                           out_subs=small_subs, out_vals=small_vals)
+    assert e.value.name == "TTV_ERR_CAPACITY"
+    bad = subs.clone()
+    bad[77, 0] = shape[0]
+    with pytest.raises(cuda_lib.TTVError) as e:
+        cuda_lib.ttv_multi(bad, vals, p.tensor.shape, p.modes, vecs, path="hash")
+    assert e.value.name == "TTV_ERR_SUBSCRIPT"
+
+
+def test_hash_empty(cuda_lib):
+    dev = "cuda"
+    subs = torch.zeros((0, 3), dtype=torch.int64, device=dev)
+    vals = torch.zeros(0, dtype=torch.float64, device=dev)
+    v = torch.ones(400, dtype=torch.float64, device=dev)
+    r = cuda_lib.ttv_single(subs, vals, (300, 400, 500), 1, v, path="hash")
+    assert r.vals.numel() == 0 and r.subs.shape == (0, 2)
