@@ -502,6 +502,7 @@ def run_serve(args, rank, world, local_rank):
     ttv.load()
     g = np.random.default_rng(args.seed + rank)
     tensors = []
+    acc_sample = []   # FP64 originals of a few small tensors, for the accuracy report
     for i in range(64):
         s = args.seed * 1000 + i
         r = S.uniform(s, 9, 2).numpy()
@@ -513,6 +514,8 @@ def run_serve(args, rank, world, local_rank):
                 break
         t = S.sptenrand(s, shp, nnz, vals="u11", device=dev)
         tensors.append((t.subs, t.vals.to(torch.float32), shp, nnz))
+        if nnz <= 2_000_000 and len(acc_sample) < 8:
+            acc_sample.append((t.subs, t.vals, shp, i))
     resident = sum(x[3] * (4 * 8 + 4) for x in tensors)
     srv = ttv.Server(budget_bytes=60 << 30, slots=8)
     plain = ttv.Server(budget_bytes=60 << 30, slots=1)
@@ -554,8 +557,29 @@ def run_serve(args, rank, world, local_rank):
     wall_plain = time.perf_counter() - t1
     pst = plain.stats()
     plain_nnz = sum(nnzs[ti] for ti, _, _ in reqs[64:64 + n_plain])
+    # accuracy of FP32 storage: the server's FP32 + compensated result against
+    # the all-FP64 compensated result of the same request (values and vector
+    # unrounded), per entry relative to A = TTV of |vals| with |x|
+    acc = []
+    for sb, v64, shp, ti in acc_sample:
+        m = int(g.integers(0, 4))
+        x64 = g.uniform(-1, 1, shp[m])
+        r32 = srv.wait(srv.submit(ids[ti], [m], [x64.astype(np.float32)], accum="compensated"))
+        xd = torch.from_numpy(x64).to(dev)
+        r64 = ttv.ttv_multi(sb, v64, shp, [m], [xd], accum="compensated")
+        ra = ttv.ttv_multi(sb, v64.abs(), shp, [m], [xd.abs()], accum="compensated")
+        A = ra.vals.double()
+        e = ((r32.vals.double() - r64.vals.double()).abs() / A.clamp_min(1e-300)).max().item()
+        subs_equal = bool(torch.equal(r32.subs, r64.subs))
+        acc.append({"nnz": int(v64.numel()), "mode": m, "max_err_over_A": e, "subs_equal": subs_equal})
     srv.close()
     plain.close()
+    accuracy = {
+        "reference": "all-FP64 compensated run of the same requests (parity tests pin it to the FP64 oracle)",
+        "requests": len(acc), "max_err_over_A": max((a["max_err_over_A"] for a in acc), default=None),
+        "bound_over_A": 2 * 2.0 ** -24 + 4 * 2.0 ** -53,
+        "subs_bit_exact": all(a["subs_equal"] for a in acc),
+    }
     line = {
         "metric": "TTV nonzeros/sec", "value": served_nnz / wall / 1e9, "unit": "GNNZ/s", "n_gpus": world,
         "steps": args.requests, "warmup": 64, "ms_per_step": 1e3 * wall / args.requests, "higher_is_better": True,
@@ -569,7 +593,7 @@ def run_serve(args, rank, world, local_rank):
         "plain": {"requests": n_plain, "throughput_rps": n_plain / wall_plain,
                   "throughput_gnnz_s": plain_nnz / wall_plain / 1e9, "p50_ms": pst["p50_us"] / 1e3,
                   "p99_ms": pst["p99_us"] / 1e3},
-        "clocks": clk,
+        "clocks": clk, "accuracy_fp32_storage": accuracy,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

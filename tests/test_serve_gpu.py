@@ -84,6 +84,30 @@ def test_server_float32_storage(cuda_lib):
     srv.close()
 
 
+@pytest.mark.parametrize("modes", [[1], [0, 3]])
+def test_server_float32_error_vs_fp64_oracle(cuda_lib, modes):
+    # FP32 value/vector storage with compensated binary64 accumulation against
+    # the FP64 oracle on the unrounded inputs: each term is perturbed by at
+    # most (n_v + 1) * 2^-24 relative (one rounding per stored factor), the
+    # accumulation adds at most 4 * 2^-53 * A.
+    dev = "cuda"
+    t = S.sptenrand(79, (200, 300, 400, 50), 200_000, vals="u11")
+    g = np.random.default_rng(5)
+    x64 = [g.uniform(-1, 1, t.shape[m]) for m in modes]
+    x32 = [x.astype(np.float32) for x in x64]
+    srv = cuda_lib.Server(budget_bytes=4 << 30, slots=2)
+    tid = srv.register(t.subs.to(dev), t.vals.to(torch.float32).to(dev), t.shape)
+    res = srv.wait(srv.submit(tid, modes, x32, accum="compensated"))
+    srv.close()
+    ref, A = oracle_ttv(t.subs, t.vals, t.shape, modes, [torch.from_numpy(x) for x in x64])
+    assert np.array_equal(res.subs.cpu().numpy(), ref[0])
+    err = np.abs(res.vals.cpu().numpy() - ref[1])
+    bound = (len(modes) + 1) * 2.0 ** -24 * A + 4 * 2.0 ** -53 * A
+    assert np.all(err <= bound), float(np.max(err / np.maximum(A, 1e-300)))
+    # the FP32 rounding is visible (the check is not vacuous) and well inside the bound
+    assert 0 < float(np.max(err / A)) < (len(modes) + 1) * 2.0 ** -24
+
+
 def test_server_budget_and_timeout(cuda_lib):
     dev = "cuda"
     t = S.sptenrand(78, (100, 100, 100), 100_000, vals="u11")
