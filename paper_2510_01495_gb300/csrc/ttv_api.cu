@@ -13,6 +13,9 @@
 namespace ttv {
 // kernels in ttv_stream.cu / ttv_sort.cu
 void launch_keys_terms(const StreamDesc& p, uint64_t* keys, double* terms, cudaStream_t stream);
+bool keys_terms_vec_applicable(const StreamDesc& p, int npass);
+void launch_keys_terms_vec(const StreamDesc& p, uint64_t* keys, double* terms, int npass, uint32_t* hist,
+                           cudaStream_t stream);
 size_t dense_smem_bytes(const StreamDesc& p, int want_presence);
 int dense_grid(const StreamDesc& p, int want_presence);
 void launch_dense(const StreamDesc& p, int want_presence, int compensated, int G, double* partials,
@@ -29,6 +32,9 @@ struct SegOut {
 void launch_seg_reduce(const uint64_t* keys, const double* vals, int64_t n, uint32_t* seg_start,
                        unsigned long long* lookback, uint32_t* ticket, uint32_t* long_list, const StreamDesc& p,
                        const SegOut& o, Status* st, cudaStream_t stream);
+size_t rbk_state_bytes(int64_t n);
+void launch_reduce_by_key(const uint64_t* keys, const double* vals, int64_t n, void* state, const StreamDesc& p,
+                          const SegOut& o, Status* st, cudaStream_t stream);
 
 bool bucket_applicable(const StreamDesc& p);
 bool hash_applicable(const StreamDesc& p);
@@ -352,6 +358,7 @@ struct WsPtrs {
     unsigned long long* seg_lookback;
     uint32_t* seg_ticket;
     uint32_t* long_list;
+    void* rbk_state;
 };
 
 static void layout(const Plan& pl, Arena& a, WsPtrs& w) {
@@ -387,10 +394,15 @@ static void layout(const Plan& pl, Arena& a, WsPtrs& w) {
         w.sb.tickets = a.take<uint32_t>(64);
         w.sb.npass = npass;
         w.sb.ntiles = ntiles;
-        w.seg_start = a.take<uint32_t>(n + 1);
-        w.seg_lookback = a.take<unsigned long long>(ntiles);
-        w.seg_ticket = a.take<uint32_t>(64);
-        w.long_list = a.take<uint32_t>(n);
+        if (pl.compensated) {
+            // compensated sums: runs found first, then summed one run per thread
+            w.seg_start = a.take<uint32_t>(n + 1);
+            w.seg_lookback = a.take<unsigned long long>(ntiles);
+            w.seg_ticket = a.take<uint32_t>(64);
+            w.long_list = a.take<uint32_t>(n);
+        } else {
+            w.rbk_state = a.take<char>(rbk_state_bytes(n));
+        }
     }
     a.off = (a.off + 255) & ~size_t(255);
 }
@@ -499,13 +511,24 @@ static int execute(const Plan& pl, ttv_out* out, const ttv_opts* o, cudaStream_t
     } else if (pl.path == TTV_PATH_HASH) {
         launch_hash(p, pl.dense_out, pl.key_bits, w.hash_ws, out->subs, ovals, cap_rows_eff, stream);
     } else {
-        launch_keys_terms(p, w.sb.keys[0], w.sb.vals[0], stream);
         SortBuffers sb = w.sb;
-        const int cur = radix_sort_pairs(sb, p.nnz, pl.key_bits, w.status, stream);
+        const int npass = (pl.key_bits + 7) / 8;
+        const bool vec = npass > 0 && p.nnz > 1 && keys_terms_vec_applicable(p, npass);
+        if (vec) {
+            // keys, terms and the digit histograms of every pass in one read
+            cudaMemsetAsync(sb.hist, 0, (size_t)npass * 256 * sizeof(uint32_t), stream);
+            launch_keys_terms_vec(p, sb.keys[0], sb.vals[0], npass, sb.hist, stream);
+        } else {
+            launch_keys_terms(p, sb.keys[0], sb.vals[0], stream);
+        }
+        const int cur = radix_sort_pairs(sb, p.nnz, pl.key_bits, w.status, stream, nullptr, vec);
         if (pl.dense_out) cudaMemsetAsync(ovals, 0, (size_t)pl.cap_vals * sizeof(double), stream);
         SegOut so{out->subs, ovals, cap_rows_eff, pl.dense_out, pl.compensated};
-        launch_seg_reduce(sb.keys[cur], sb.vals[cur], p.nnz, w.seg_start, w.seg_lookback, w.seg_ticket,
-                          w.long_list, p, so, w.status, stream);
+        if (pl.compensated)
+            launch_seg_reduce(sb.keys[cur], sb.vals[cur], p.nnz, w.seg_start, w.seg_lookback, w.seg_ticket,
+                              w.long_list, p, so, w.status, stream);
+        else
+            launch_reduce_by_key(sb.keys[cur], sb.vals[cur], p.nnz, w.rbk_state, p, so, w.status, stream);
     }
     if (pl.order0) {
         // scalar result: nnz 1 whatever the input

@@ -339,7 +339,9 @@ size_t sort_workspace_bytes(int64_t n, int bits);
 // buffer (0/1) holds the result.  With n_dev, the pair count is
 // min(n, *n_dev), read on the device (n is then the upper bound the buffers
 // and grids are sized for).
+// hist_ready: sb.hist already holds the digit counts of every pass (the
+// specialised key kernel counts them while it writes the keys).
 int radix_sort_pairs(SortBuffers& sb, int64_t n, int bits, Status* st, cudaStream_t stream,
-                     const unsigned long long* n_dev = nullptr);
+                     const unsigned long long* n_dev = nullptr, bool hist_ready = false);
 
 }  // namespace ttv

@@ -120,7 +120,7 @@ struct OnesweepSmem {
     double vals[kSortTile];
 };
 
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint64_t* __restrict__ keys_in,
+__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const uint64_t* __restrict__ keys_in,
                                                            const double* __restrict__ vals_in,
                                                            uint64_t* __restrict__ keys_out,
                                                            double* __restrict__ vals_out, int64_t n, int shift,
@@ -141,37 +141,34 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint64_t* __res
     if (n_dev) n = min(n, (int64_t)*n_dev);
     if (base >= n) return;
 
+    // Keys first: ranking needs only them, and they go to shared memory
+    // before the values are loaded, so that at most 16 keys or 16 values
+    // (plus one packed word per item) are live per thread and three CTAs fit
+    // on an SM.
     uint64_t k[kSortItems];
-    double v[kSortItems];
-    uint32_t dig[kSortItems];
-    uint32_t rank[kSortItems];
+    uint32_t rd[kSortItems];     // rank << 9 | digit, then the staging slot
+    const int64_t wbase = base + warp * (kSortItems * 32) + lane;
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
-        const int64_t idx = base + warp * (kSortItems * 32) + i * 32 + lane;
-        if (idx < n) {
-            k[i] = __ldcs(keys_in + idx);
-            v[i] = __ldcs(vals_in + idx);
-            dig[i] = (uint32_t)(k[i] >> shift) & (kRadix - 1);
-        } else {
-            k[i] = 0;
-            v[i] = 0.0;
-            dig[i] = kRadix;     // padding bucket, never published or written
-        }
+        const int64_t idx = wbase + i * 32;
+        k[i] = idx < n ? __ldcs(keys_in + idx) : 0ull;
     }
     // Warp-level multi-split: rank of each item among equal digits of its warp.
     uint32_t* wh = sm.whist + warp * kHistStride;
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
-        const uint32_t mask = __match_any_sync(0xffffffffu, dig[i]);
+        // padding bucket kRadix for absent items: never published or written
+        const uint32_t dig = wbase + i * 32 < n ? (uint32_t)(k[i] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
+        const uint32_t mask = __match_any_sync(0xffffffffu, dig);
         const int leader = __ffs(mask) - 1;
         uint32_t b = 0;
         if (lane == leader) {
-            b = wh[dig[i]];
-            wh[dig[i]] = b + __popc(mask);
+            b = wh[dig];
+            wh[dig] = b + __popc(mask);
         }
         b = __shfl_sync(0xffffffffu, b, leader);
-        rank[i] = b + __popc(mask & lt);
+        rd[i] = (b + __popc(mask & lt)) << 9 | dig;
         __syncwarp();
     }
     __syncthreads();
@@ -186,6 +183,28 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint64_t* __res
     }
     uint32_t tile_total;
     sm.tile_start[tid] = block_exclusive_scan_256(cnt, sm.warp_tot, tile_total);
+    __syncthreads();
+
+    // Keys into shared memory in digit order (stable); keep each item's slot.
+    constexpr uint32_t kAbsent = 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const uint32_t dig = rd[i] & 511u;
+        if (dig < (uint32_t)kRadix) {
+            const uint32_t pos = sm.tile_start[dig] + sm.whist[warp * kHistStride + dig] + (rd[i] >> 9);
+            sm.keys[pos] = k[i];
+            rd[i] = pos;
+        } else {
+            rd[i] = kAbsent;
+        }
+    }
+    // Values: loads issued now, consumed after the look-back.
+    double v[kSortItems];
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const int64_t idx = wbase + i * 32;
+        v[i] = idx < n ? __ldcs(vals_in + idx) : 0.0;
+    }
 
     // Decoupled look-back across tiles for digit t.
     uint32_t* my = lookback + (size_t)tile * kRadix + tid;
@@ -212,18 +231,12 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint64_t* __res
         st_relaxed(my, kFlagInc | ((exclusive + cnt) & kCountMask));
     }
     sm.gbase[tid] = digit_off[tid] + exclusive;
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i)
+        if (rd[i] != kAbsent) sm.vals[rd[i]] = v[i];
     __syncthreads();
 
-    // Scatter into shared memory in digit order (stable), then out.
-#pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-        if (dig[i] < (uint32_t)kRadix) {
-            const uint32_t pos = sm.tile_start[dig[i]] + sm.whist[warp * kHistStride + dig[i]] + rank[i];
-            sm.keys[pos] = k[i];
-            sm.vals[pos] = v[i];
-        }
-    }
-    __syncthreads();
+    // Out: consecutive threads write consecutive slots of each digit run.
     const int tile_n = (int)min((int64_t)kSortTile, n - base);
     for (int j = tid; j < tile_n; j += kSortThreads) {
         const uint64_t kk = sm.keys[j];
@@ -246,23 +259,27 @@ size_t sort_workspace_bytes(int64_t n, int bits) {
 }
 
 int radix_sort_pairs(SortBuffers& sb, int64_t n, int bits, Status* st, cudaStream_t stream,
-                     const unsigned long long* n_dev) {
+                     const unsigned long long* n_dev, bool hist_ready) {
     const int npass = bits <= 0 ? 0 : (bits + kRadixBits - 1) / kRadixBits;
     if (npass == 0 || n <= 1) return 0;
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    cudaMemsetAsync(sb.hist, 0, (size_t)npass * kRadix * sizeof(uint32_t), stream);
+    if (!hist_ready) cudaMemsetAsync(sb.hist, 0, (size_t)npass * kRadix * sizeof(uint32_t), stream);
     cudaMemsetAsync(sb.lookback, 0, (size_t)npass * ntiles * kRadix * sizeof(uint32_t), stream);
     cudaMemsetAsync(sb.tickets, 0, 64 * sizeof(uint32_t), stream);
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int hblocks = (int)std::min<int64_t>((int64_t)nsm * 4, (n + 255) / 256);
-    TTV_LAUNCH("radix_hist", stream, k_radix_hist<<<hblocks, 256, 0, stream>>>(sb.keys[0], n, npass, sb.hist, n_dev));
+    if (!hist_ready)
+        TTV_LAUNCH("radix_hist", stream, k_radix_hist<<<hblocks, 256, 0, stream>>>(sb.keys[0], n, npass, sb.hist, n_dev));
     TTV_LAUNCH("radix_hist_scan", stream, k_radix_hist_scan<<<1, 256, 0, stream>>>(sb.hist, npass));
     const size_t smem = sizeof(OnesweepSmem);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // all of the unified L1 as shared memory: three 75 KB CTAs per SM
+        cudaFuncSetAttribute(k_onesweep, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
         attr_set = true;
     }
     int cur = 0;
@@ -445,6 +462,374 @@ __global__ void __launch_bounds__(256) k_long_seg(const uint64_t* __restrict__ k
             o.vals[o.dense ? (int64_t)keys[s0] : (int64_t)j] = r;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Reduce-by-key of sorted pairs (binary64 accumulation), in three passes
+// with no waiting between tiles.
+//
+// A pair is a head when its key differs from its predecessor's.  Every
+// thread takes 8 consecutive pairs (16-byte loads) and summarises them as
+// (heads, has_head, open value: the sum since its last head, or of all its
+// pairs when it has none).  Summaries combine left to right by
+//     (ca, fa, va) . (cb, fb, vb) = (ca + cb, fa | fb, fb ? vb : va + vb).
+//   k_rbk_tiles  one summary per 2048-pair tile (fixed shuffle tree);
+//   k_rbk_scan   one CTA: exclusive scan of the tile summaries (each thread
+//                a fixed chunk, then a fixed tree over the chunks): heads
+//                before each tile and the open value entering it;
+//   k_rbk_emit   the tile again: in-tile exclusive scan, then every head
+//                closes the segment before it (the last pair closes the
+//                last one): key and sum staged in shared memory at the
+//                segment's row within the tile, then written out coalesced,
+//                the key delinearised into the surviving subscripts.
+// Every combination happens in an order fixed by the data layout alone, so
+// the result is bit-identical from run to run.
+constexpr int kRbkThreads = 256;
+constexpr int kRbkItems = 8;
+constexpr int kRbkTile = kRbkThreads * kRbkItems;
+constexpr int kRbkScanThreads = 1024;
+
+struct RbkSum {                  // a summary: value first for alignment
+    double val;
+    uint32_t cnt;
+    uint32_t flag;
+};
+
+__device__ __forceinline__ void seg_combine(uint32_t ca, uint32_t fa, double va, uint32_t& cb, uint32_t& fb,
+                                            double& vb) {
+    cb = ca + cb;
+    vb = fb ? vb : va + vb;
+    fb = fa | fb;
+}
+
+// This thread's pairs of tile `tile` and their summary.
+struct RbkPairs {
+    uint64_t k[kRbkItems];
+    double v[kRbkItems];
+    uint64_t prev0;
+    int nmine;
+    int64_t g0;
+    uint32_t heads, cnt, flag;
+    double open;
+};
+
+__device__ __forceinline__ void rbk_load(const uint64_t* __restrict__ keys, const double* __restrict__ vals,
+                                         int64_t n, int64_t tile, RbkPairs& r) {
+    r.g0 = tile * kRbkTile + (int64_t)threadIdx.x * kRbkItems;
+    r.nmine = (int)max((int64_t)0, min((int64_t)kRbkItems, n - r.g0));
+    if (r.nmine == kRbkItems) {
+        // the pair buffers are 16-byte aligned and g0 is a multiple of 8
+#pragma unroll
+        for (int q = 0; q < kRbkItems / 2; ++q) {
+            const ulonglong2 kk = __ldcs(reinterpret_cast<const ulonglong2*>(keys + r.g0) + q);
+            const double2 vv = __ldcs(reinterpret_cast<const double2*>(vals + r.g0) + q);
+            r.k[2 * q] = kk.x;
+            r.k[2 * q + 1] = kk.y;
+            r.v[2 * q] = vv.x;
+            r.v[2 * q + 1] = vv.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kRbkItems; ++i) {
+            r.k[i] = i < r.nmine ? keys[r.g0 + i] : ~0ull;
+            r.v[i] = i < r.nmine ? vals[r.g0 + i] : 0.0;
+        }
+    }
+    r.prev0 = (r.g0 > 0 && r.nmine > 0) ? keys[r.g0 - 1] : ~0ull;   // keys are < 2^64 - 1
+    r.heads = 0;
+    r.cnt = 0;
+    r.flag = 0;
+    r.open = 0.0;
+    uint64_t prev = r.prev0;
+#pragma unroll
+    for (int i = 0; i < kRbkItems; ++i) {
+        if (i < r.nmine) {
+            if (r.k[i] != prev || r.g0 + i == 0) {
+                r.heads |= 1u << i;
+                ++r.cnt;
+                r.flag = 1;
+                r.open = r.v[i];
+            } else {
+                r.open = r.open + r.v[i];
+            }
+            prev = r.k[i];
+        }
+    }
+}
+
+// Block scan of the thread summaries: each thread gets its exclusive prefix
+// within the tile; returns the tile total (all threads).
+struct RbkScanSmem {
+    uint32_t cnt[kRbkThreads / 32];
+    uint32_t flag[kRbkThreads / 32];
+    double val[kRbkThreads / 32];
+};
+
+__device__ __forceinline__ void rbk_block_scan(const RbkPairs& r, RbkScanSmem& ss, uint32_t& xc, uint32_t& xf,
+                                               double& xv, uint32_t& tc, uint32_t& tf, double& tv) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t c = r.cnt, f = r.flag;
+    double v = r.open;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t c2 = __shfl_up_sync(0xffffffffu, c, off);
+        const uint32_t f2 = __shfl_up_sync(0xffffffffu, f, off);
+        const double v2 = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) seg_combine(c2, f2, v2, c, f, v);
+    }
+    if (lane == 31) {
+        ss.cnt[warp] = c;
+        ss.flag[warp] = f;
+        ss.val[warp] = v;
+    }
+    xc = __shfl_up_sync(0xffffffffu, c, 1);
+    xf = __shfl_up_sync(0xffffffffu, f, 1);
+    xv = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 0) { xc = 0; xf = 0; xv = 0.0; }
+    __syncthreads();
+    // warp prefix, left to right over the 8 warps (every thread computes it)
+    uint32_t pc = 0, pf = 0;
+    double pv = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRbkThreads / 32; ++w) {
+        if (w == warp) {
+            if (w > 0) seg_combine(pc, pf, pv, xc, xf, xv);
+        }
+        uint32_t cw = ss.cnt[w], fw = ss.flag[w];
+        double vw = ss.val[w];
+        if (w > 0) seg_combine(pc, pf, pv, cw, fw, vw);
+        pc = cw;
+        pf = fw;
+        pv = vw;
+    }
+    tc = pc;
+    tf = pf;
+    tv = pv;
+}
+
+__global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles(const uint64_t* __restrict__ keys,
+                                                           const double* __restrict__ vals, int64_t n,
+                                                           RbkSum* __restrict__ tiles) {
+    __shared__ RbkScanSmem ss;
+    RbkPairs r;
+    rbk_load(keys, vals, n, blockIdx.x, r);
+    uint32_t xc, xf, tc, tf;
+    double xv, tv;
+    rbk_block_scan(r, ss, xc, xf, xv, tc, tf, tv);
+    if (threadIdx.x == 0) {
+        RbkSum t;
+        t.val = tv;
+        t.cnt = tc;
+        t.flag = tf;
+        tiles[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of the tile summaries; prefix[t] = (heads before tile t,
+// open value entering it); the total head count is the result size.
+__global__ void __launch_bounds__(kRbkScanThreads) k_rbk_scan(const RbkSum* __restrict__ tiles, int64_t ntiles,
+                                                              RbkSum* __restrict__ prefix,
+                                                              unsigned long long* __restrict__ heads_before,
+                                                              Status* st) {
+    __shared__ uint32_t s_flag[kRbkScanThreads / 32];
+    __shared__ double s_val[kRbkScanThreads / 32];
+    __shared__ unsigned long long s_base[kRbkScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t per = (ntiles + kRbkScanThreads - 1) / kRbkScanThreads;
+    const int64_t lo = min(ntiles, (int64_t)tid * per), hi = min(ntiles, lo + per);
+    // chunk summary, left to right (head counts in 64 bits across chunks);
+    // loads in batches of 8 so that they are in flight together
+    constexpr int kB = 8;
+    unsigned long long cc = 0;
+    uint32_t cf = 0;
+    double cv = 0.0;
+    for (int64_t t0 = lo; t0 < hi; t0 += kB) {
+        RbkSum a[kB];
+#pragma unroll
+        for (int b = 0; b < kB; ++b) a[b] = t0 + b < hi ? tiles[t0 + b] : RbkSum{0.0, 0u, 0u};
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+            if (t0 + b < hi) {
+                cc += a[b].cnt;
+                cv = a[b].flag ? a[b].val : cv + a[b].val;
+                cf |= a[b].flag;
+            }
+        }
+    }
+    // exclusive scan over chunks: counts by warp sums, values by a fixed tree
+    unsigned long long c = cc;
+    uint32_t f = cf;
+    double v = cv;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long c2 = __shfl_up_sync(0xffffffffu, c, off);
+        const uint32_t f2 = __shfl_up_sync(0xffffffffu, f, off);
+        const double v2 = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) {
+            c = c2 + c;
+            v = f ? v : v2 + v;
+            f = f2 | f;
+        }
+    }
+    if (lane == 31) {
+        s_base[warp] = c;
+        s_flag[warp] = f;
+        s_val[warp] = v;
+    }
+    unsigned long long xc = __shfl_up_sync(0xffffffffu, c, 1);
+    uint32_t xf = __shfl_up_sync(0xffffffffu, f, 1);
+    double xv = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 0) { xc = 0; xf = 0; xv = 0.0; }
+    __syncthreads();
+    unsigned long long pc = 0;
+    uint32_t pf = 0;
+    double pv = 0.0;
+    for (int w = 0; w < warp; ++w) {
+        const unsigned long long cw = s_base[w];
+        const uint32_t fw = s_flag[w];
+        const double vw = s_val[w];
+        pc = pc + cw;
+        pv = fw ? vw : pv + vw;
+        pf = pf | fw;
+    }
+    // this chunk's exclusive prefix = warp prefix . lane-exclusive
+    unsigned long long rc = pc + xc;
+    double rv = xf ? xv : pv + xv;
+    for (int64_t t0 = lo; t0 < hi; t0 += kB) {
+        RbkSum a[kB];
+#pragma unroll
+        for (int b = 0; b < kB; ++b) a[b] = t0 + b < hi ? tiles[t0 + b] : RbkSum{0.0, 0u, 0u};
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+            if (t0 + b < hi) {
+                RbkSum out;
+                out.val = rv;
+                out.cnt = 0;
+                out.flag = 0;
+                prefix[t0 + b] = out;
+                heads_before[t0 + b] = rc;
+                rc += a[b].cnt;
+                rv = a[b].flag ? a[b].val : rv + a[b].val;
+            }
+        }
+    }
+    if (hi == ntiles && lo < hi) st->nnz_out = rc;
+}
+
+struct RbkEmitSmem {
+    uint64_t row_key[kRbkTile + 1];        // closed segments of this tile, by row
+    double row_val[kRbkTile + 1];
+    RbkScanSmem ss;
+};
+
+__global__ void __launch_bounds__(kRbkThreads, 3) k_rbk_emit(const uint64_t* __restrict__ keys,
+                                                             const double* __restrict__ vals, int64_t n,
+                                                             const RbkSum* __restrict__ prefix,
+                                                             const unsigned long long* __restrict__ heads_before,
+                                                             StreamDesc p, SegOut o, Status* st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RbkEmitSmem& sm = *reinterpret_cast<RbkEmitSmem*>(smem_raw);
+    const int64_t tile = blockIdx.x;
+    const int64_t ntiles = (n + kRbkTile - 1) / kRbkTile;
+    RbkPairs r;
+    rbk_load(keys, vals, n, tile, r);
+    uint32_t xc, xf, tc, tf;
+    double xv, tv;
+    rbk_block_scan(r, sm.ss, xc, xf, xv, tc, tf, tv);
+    const double carry = prefix[tile].val;
+    const unsigned long long hb = heads_before[tile];
+    double run = xf ? xv : carry + xv;
+    // a head at tile-local head index h closes the segment at row h - first
+    // of this tile (first = 1 in tile 0, whose first head closes nothing)
+    const int first = tile == 0 ? 1 : 0;
+    int h = (int)xc;
+    uint64_t prev = r.prev0;
+#pragma unroll
+    for (int i = 0; i < kRbkItems; ++i) {
+        if (i < r.nmine) {
+            if ((r.heads >> i) & 1u) {
+                if (r.g0 + i > 0) {
+                    sm.row_key[h - first] = prev;
+                    sm.row_val[h - first] = run;
+                }
+                ++h;
+                run = r.v[i];
+            } else {
+                run = run + r.v[i];
+            }
+            prev = r.k[i];
+        }
+    }
+    const bool last_tile = tile == ntiles - 1;
+    if (r.nmine > 0 && r.g0 + r.nmine == n) {   // the last pair closes the last segment
+        sm.row_key[h - first] = prev;
+        sm.row_val[h - first] = run;
+    }
+    __syncthreads();
+    const int nrows = (int)tc - first + (last_tile ? 1 : 0);
+    const int64_t row0 = (int64_t)hb - 1 + first;
+    const bool even_rows = (p.nr % 2 == 0) && ((reinterpret_cast<uintptr_t>(o.subs) & 15) == 0);
+    for (int q = threadIdx.x; q < nrows; q += kRbkThreads) {
+        const uint64_t key = sm.row_key[q];
+        const double val = sm.row_val[q];
+        const int64_t row = row0 + q;
+        if (o.dense) {
+            o.vals[(int64_t)key] = val;
+        } else if (row < o.cap_rows) {
+            int64_t* dst = o.subs + row * p.nr;
+            if (even_rows) {
+                // 16-byte stores: the row starts on a 16-byte boundary
+                // delinearise with every index known at compile time, so
+                // that the subscripts stay in registers
+                int64_t sub[kMaxD];
+                uint64_t kk = key;
+#pragma unroll
+                for (int j = kMaxD - 1; j >= 0; --j) {
+                    sub[j] = 0;
+                    if (j < p.nr) {
+                        const uint64_t nj = (uint64_t)p.rshape[j];
+                        const uint64_t q = udiv_invariant(kk, p.rmagic[j], p.rsh[j]);
+                        sub[j] = (int64_t)(kk - q * nj);
+                        kk = q;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kMaxD; j += 2)
+                    if (j < p.nr) reinterpret_cast<longlong2*>(dst)[j / 2] = make_longlong2(sub[j], sub[j + 1]);
+            } else {
+                delinearise(p, key, dst);
+            }
+            o.vals[row] = val;
+        } else {
+            set_error(st, kErrCapacity);
+        }
+    }
+}
+
+size_t rbk_state_bytes(int64_t n) {
+    const int64_t ntiles = (std::max<int64_t>(n, 1) + kRbkTile - 1) / kRbkTile;
+    return (size_t)ntiles * (2 * sizeof(RbkSum) + sizeof(unsigned long long)) + 512;
+}
+
+void launch_reduce_by_key(const uint64_t* keys, const double* vals, int64_t n, void* state, const StreamDesc& p,
+                          const SegOut& o, Status* st, cudaStream_t stream) {
+    if (n <= 0) return;
+    const int64_t ntiles = (n + kRbkTile - 1) / kRbkTile;
+    RbkSum* tiles = static_cast<RbkSum*>(state);
+    RbkSum* prefix = tiles + ntiles;
+    unsigned long long* hb = reinterpret_cast<unsigned long long*>(prefix + ntiles);
+    const size_t smem = sizeof(RbkEmitSmem);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_rbk_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_rbk_emit, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        attr_set = true;
+    }
+    TTV_LAUNCH("rbk_tiles", stream, k_rbk_tiles<<<(unsigned)ntiles, kRbkThreads, 0, stream>>>(keys, vals, n, tiles));
+    TTV_LAUNCH("rbk_scan", stream, k_rbk_scan<<<1, kRbkScanThreads, 0, stream>>>(tiles, ntiles, prefix, hb, st));
+    TTV_LAUNCH("rbk_emit", stream,
+               k_rbk_emit<<<(unsigned)ntiles, kRbkThreads, smem, stream>>>(keys, vals, n, prefix, hb, p, o, st));
 }
 
 void launch_seg_reduce(const uint64_t* keys, const double* vals, int64_t n, uint32_t* seg_start,

@@ -341,3 +341,33 @@ def test_hash_empty(cuda_lib):
     v = torch.ones(400, dtype=torch.float64, device=dev)
     r = cuda_lib.ttv_single(subs, vals, (300, 400, 500), 1, v, path="hash")
     assert r.vals.numel() == 0 and r.subs.shape == (0, 2)
+
+
+# ---- one-pass reduce-by-key after the sort -------------------------------------------
+
+@pytest.mark.parametrize("fmt", ["sparse", "dense"])
+def test_sort_segments_spanning_many_tiles(cuda_lib, fmt):
+    # one surviving tuple 300 000 times (73 tiles of 4096 pairs: the look-back
+    # folds more tiles than it keeps in registers), a second long run, and
+    # singletons around them; bit-identical from run to run
+    g = np.random.default_rng(8)
+    n = 500_000
+    subs = np.stack([g.integers(0, 40, n), g.integers(0, 30, n), g.integers(0, 20, n)], axis=1)
+    subs[:300_000, 0] = 7
+    subs[:300_000, 2] = 3
+    subs[300_000:350_000, 0] = 39
+    subs[300_000:350_000, 2] = 19
+    vals = g.uniform(-1, 1, n)
+    x = g.uniform(-1, 1, 30)
+    p = S.Problem(S.SparseTensor(torch.from_numpy(subs), torch.from_numpy(vals), (40, 30, 20)), [1],
+                  [torch.from_numpy(x)], name="long_runs")
+    r1 = run_case(cuda_lib, p, path="sort", fmt=fmt)
+    subs_d, vals_d, vecs_d = to_device(p)
+    r2 = cuda_lib.ttv_multi(subs_d, vals_d, p.tensor.shape, p.modes, vecs_d, path="sort", fmt=fmt)
+    assert torch.equal(r1.vals, r2.vals)
+
+
+@pytest.mark.parametrize("nnz", [1, 2, 4095, 4096, 4097, 8192, 12_289])
+def test_sort_tile_edges(cuda_lib, nnz):
+    p = rand_problem(500 + nnz, (300, 200, 100), nnz, [1])
+    run_case(cuda_lib, p, path="sort")
