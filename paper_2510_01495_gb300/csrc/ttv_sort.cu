@@ -474,9 +474,11 @@ __global__ void __launch_bounds__(256) k_long_seg(const uint64_t* __restrict__ k
 // pairs when it has none).  Summaries combine left to right by
 //     (ca, fa, va) . (cb, fb, vb) = (ca + cb, fa | fb, fb ? vb : va + vb).
 //   k_rbk_tiles  one summary per 2048-pair tile (fixed shuffle tree);
-//   k_rbk_scan   one CTA: exclusive scan of the tile summaries (each thread
+//   k_rbk_groups one warp per 32 tiles: in-group exclusive prefixes and the
+//                group summary (fixed shuffle tree);
+//   k_rbk_scan   one CTA: exclusive scan of the group summaries (each thread
 //                a fixed chunk, then a fixed tree over the chunks): heads
-//                before each tile and the open value entering it;
+//                before each group and the open value entering it;
 //   k_rbk_emit   the tile again: in-tile exclusive scan, then every head
 //                closes the segment before it (the last pair closes the
 //                last one): key and sum staged in shared memory at the
@@ -625,36 +627,57 @@ __global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles(const uint64_t* __res
     }
 }
 
-// Exclusive scan of the tile summaries; prefix[t] = (heads before tile t,
-// open value entering it); the total head count is the result size.
-__global__ void __launch_bounds__(kRbkScanThreads) k_rbk_scan(const RbkSum* __restrict__ tiles, int64_t ntiles,
-                                                              RbkSum* __restrict__ prefix,
-                                                              unsigned long long* __restrict__ heads_before,
+// One warp per group of 32 tiles: each tile's exclusive prefix within the
+// group (ingroup[t]) and the group's summary (groups[g]).
+constexpr int kRbkGroup = 32;
+
+__global__ void __launch_bounds__(256) k_rbk_groups(const RbkSum* __restrict__ tiles, int64_t ntiles,
+                                                    RbkSum* __restrict__ ingroup, RbkSum* __restrict__ groups,
+                                                    int64_t ngroups) {
+    const int lane = threadIdx.x & 31;
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= ngroups) return;
+    const int64_t t = g * kRbkGroup + lane;
+    RbkSum a = t < ntiles ? tiles[t] : RbkSum{0.0, 0u, 0u};
+    uint32_t c = a.cnt, f = a.flag;
+    double v = a.val;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t c2 = __shfl_up_sync(0xffffffffu, c, off);
+        const uint32_t f2 = __shfl_up_sync(0xffffffffu, f, off);
+        const double v2 = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) seg_combine(c2, f2, v2, c, f, v);
+    }
+    uint32_t xc = __shfl_up_sync(0xffffffffu, c, 1);
+    uint32_t xf = __shfl_up_sync(0xffffffffu, f, 1);
+    double xv = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 0) { xc = 0; xf = 0; xv = 0.0; }
+    if (t < ntiles) ingroup[t] = RbkSum{xv, xc, xf};
+    if (lane == 31) groups[g] = RbkSum{v, c, f};
+}
+
+// Exclusive scan of the group summaries; gprefix[g] = open value entering
+// group g, gheads[g] = heads before it; the total head count is the result
+// size.
+__global__ void __launch_bounds__(kRbkScanThreads) k_rbk_scan(const RbkSum* __restrict__ groups, int64_t ngroups,
+                                                              RbkSum* __restrict__ gprefix,
+                                                              unsigned long long* __restrict__ gheads,
                                                               Status* st) {
     __shared__ uint32_t s_flag[kRbkScanThreads / 32];
     __shared__ double s_val[kRbkScanThreads / 32];
     __shared__ unsigned long long s_base[kRbkScanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t per = (ntiles + kRbkScanThreads - 1) / kRbkScanThreads;
-    const int64_t lo = min(ntiles, (int64_t)tid * per), hi = min(ntiles, lo + per);
-    // chunk summary, left to right (head counts in 64 bits across chunks);
-    // loads in batches of 8 so that they are in flight together
-    constexpr int kB = 8;
+    const int64_t per = (ngroups + kRbkScanThreads - 1) / kRbkScanThreads;
+    const int64_t lo = min(ngroups, (int64_t)tid * per), hi = min(ngroups, lo + per);
+    // chunk summary, left to right (head counts in 64 bits)
     unsigned long long cc = 0;
     uint32_t cf = 0;
     double cv = 0.0;
-    for (int64_t t0 = lo; t0 < hi; t0 += kB) {
-        RbkSum a[kB];
-#pragma unroll
-        for (int b = 0; b < kB; ++b) a[b] = t0 + b < hi ? tiles[t0 + b] : RbkSum{0.0, 0u, 0u};
-#pragma unroll
-        for (int b = 0; b < kB; ++b) {
-            if (t0 + b < hi) {
-                cc += a[b].cnt;
-                cv = a[b].flag ? a[b].val : cv + a[b].val;
-                cf |= a[b].flag;
-            }
-        }
+    for (int64_t t = lo; t < hi; ++t) {
+        const RbkSum a = groups[t];
+        cc += a.cnt;
+        cv = a.flag ? a.val : cv + a.val;
+        cf |= a.flag;
     }
     // exclusive scan over chunks: counts by warp sums, values by a fixed tree
     unsigned long long c = cc;
@@ -682,38 +705,22 @@ __global__ void __launch_bounds__(kRbkScanThreads) k_rbk_scan(const RbkSum* __re
     if (lane == 0) { xc = 0; xf = 0; xv = 0.0; }
     __syncthreads();
     unsigned long long pc = 0;
-    uint32_t pf = 0;
     double pv = 0.0;
     for (int w = 0; w < warp; ++w) {
-        const unsigned long long cw = s_base[w];
-        const uint32_t fw = s_flag[w];
-        const double vw = s_val[w];
-        pc = pc + cw;
-        pv = fw ? vw : pv + vw;
-        pf = pf | fw;
+        pc = pc + s_base[w];
+        pv = s_flag[w] ? s_val[w] : pv + s_val[w];
     }
     // this chunk's exclusive prefix = warp prefix . lane-exclusive
     unsigned long long rc = pc + xc;
     double rv = xf ? xv : pv + xv;
-    for (int64_t t0 = lo; t0 < hi; t0 += kB) {
-        RbkSum a[kB];
-#pragma unroll
-        for (int b = 0; b < kB; ++b) a[b] = t0 + b < hi ? tiles[t0 + b] : RbkSum{0.0, 0u, 0u};
-#pragma unroll
-        for (int b = 0; b < kB; ++b) {
-            if (t0 + b < hi) {
-                RbkSum out;
-                out.val = rv;
-                out.cnt = 0;
-                out.flag = 0;
-                prefix[t0 + b] = out;
-                heads_before[t0 + b] = rc;
-                rc += a[b].cnt;
-                rv = a[b].flag ? a[b].val : rv + a[b].val;
-            }
-        }
+    for (int64_t t = lo; t < hi; ++t) {
+        gprefix[t] = RbkSum{rv, 0u, 0u};
+        gheads[t] = rc;
+        const RbkSum a = groups[t];
+        rc += a.cnt;
+        rv = a.flag ? a.val : rv + a.val;
     }
-    if (hi == ntiles && lo < hi) st->nnz_out = rc;
+    if (hi == ngroups && lo < hi) st->nnz_out = rc;
 }
 
 struct RbkEmitSmem {
@@ -724,8 +731,9 @@ struct RbkEmitSmem {
 
 __global__ void __launch_bounds__(kRbkThreads, 3) k_rbk_emit(const uint64_t* __restrict__ keys,
                                                              const double* __restrict__ vals, int64_t n,
-                                                             const RbkSum* __restrict__ prefix,
-                                                             const unsigned long long* __restrict__ heads_before,
+                                                             const RbkSum* __restrict__ ingroup,
+                                                             const RbkSum* __restrict__ gprefix,
+                                                             const unsigned long long* __restrict__ gheads,
                                                              StreamDesc p, SegOut o, Status* st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RbkEmitSmem& sm = *reinterpret_cast<RbkEmitSmem*>(smem_raw);
@@ -736,8 +744,11 @@ __global__ void __launch_bounds__(kRbkThreads, 3) k_rbk_emit(const uint64_t* __r
     uint32_t xc, xf, tc, tf;
     double xv, tv;
     rbk_block_scan(r, sm.ss, xc, xf, xv, tc, tf, tv);
-    const double carry = prefix[tile].val;
-    const unsigned long long hb = heads_before[tile];
+    // open value entering the tile: group prefix . in-group prefix
+    const RbkSum ig = ingroup[tile];
+    const int64_t g = tile / kRbkGroup;
+    const double carry = ig.flag ? ig.val : gprefix[g].val + ig.val;
+    const unsigned long long hb = gheads[g] + ig.cnt;
     double run = xf ? xv : carry + xv;
     // a head at tile-local head index h closes the segment at row h - first
     // of this tile (first = 1 in tile 0, whose first head closes nothing)
@@ -808,16 +819,21 @@ __global__ void __launch_bounds__(kRbkThreads, 3) k_rbk_emit(const uint64_t* __r
 
 size_t rbk_state_bytes(int64_t n) {
     const int64_t ntiles = (std::max<int64_t>(n, 1) + kRbkTile - 1) / kRbkTile;
-    return (size_t)ntiles * (2 * sizeof(RbkSum) + sizeof(unsigned long long)) + 512;
+    const int64_t ngroups = (ntiles + kRbkGroup - 1) / kRbkGroup;
+    return (size_t)ntiles * 2 * sizeof(RbkSum) +
+           (size_t)ngroups * (2 * sizeof(RbkSum) + sizeof(unsigned long long)) + 512;
 }
 
 void launch_reduce_by_key(const uint64_t* keys, const double* vals, int64_t n, void* state, const StreamDesc& p,
                           const SegOut& o, Status* st, cudaStream_t stream) {
     if (n <= 0) return;
     const int64_t ntiles = (n + kRbkTile - 1) / kRbkTile;
+    const int64_t ngroups = (ntiles + kRbkGroup - 1) / kRbkGroup;
     RbkSum* tiles = static_cast<RbkSum*>(state);
-    RbkSum* prefix = tiles + ntiles;
-    unsigned long long* hb = reinterpret_cast<unsigned long long*>(prefix + ntiles);
+    RbkSum* ingroup = tiles + ntiles;
+    RbkSum* groups = ingroup + ntiles;
+    RbkSum* gprefix = groups + ngroups;
+    unsigned long long* gheads = reinterpret_cast<unsigned long long*>(gprefix + ngroups);
     const size_t smem = sizeof(RbkEmitSmem);
     static bool attr_set = false;
     if (!attr_set) {
@@ -827,9 +843,14 @@ void launch_reduce_by_key(const uint64_t* keys, const double* vals, int64_t n, v
         attr_set = true;
     }
     TTV_LAUNCH("rbk_tiles", stream, k_rbk_tiles<<<(unsigned)ntiles, kRbkThreads, 0, stream>>>(keys, vals, n, tiles));
-    TTV_LAUNCH("rbk_scan", stream, k_rbk_scan<<<1, kRbkScanThreads, 0, stream>>>(tiles, ntiles, prefix, hb, st));
+    TTV_LAUNCH("rbk_groups", stream,
+               k_rbk_groups<<<(unsigned)((ngroups * 32 + 255) / 256), 256, 0, stream>>>(tiles, ntiles, ingroup, groups,
+                                                                                      ngroups));
+    TTV_LAUNCH("rbk_scan", stream,
+               k_rbk_scan<<<1, kRbkScanThreads, 0, stream>>>(groups, ngroups, gprefix, gheads, st));
     TTV_LAUNCH("rbk_emit", stream,
-               k_rbk_emit<<<(unsigned)ntiles, kRbkThreads, smem, stream>>>(keys, vals, n, prefix, hb, p, o, st));
+               k_rbk_emit<<<(unsigned)ntiles, kRbkThreads, smem, stream>>>(keys, vals, n, ingroup, gprefix, gheads, p,
+                                                                            o, st));
 }
 
 void launch_seg_reduce(const uint64_t* keys, const double* vals, int64_t n, uint32_t* seg_start,
