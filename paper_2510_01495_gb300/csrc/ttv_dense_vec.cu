@@ -16,7 +16,7 @@
 namespace ttv {
 
 constexpr int kVecThreads = 256;
-constexpr int kVecPairs = 2;       // pairs of nonzeros per thread per iteration
+constexpr int kVecPairs = 1;       // pairs of nonzeros per thread per iteration (59 registers: 4 CTAs per SM)
 
 template <int D, bool kIntP>
 __device__ __forceinline__ void dense_item(const StreamDesc& p, const double* sv, const SigEntry* sve,
@@ -62,7 +62,7 @@ __device__ __forceinline__ void dense_item(const StreamDesc& p, const double* sv
 }
 
 template <int D, bool kSoA, bool kIntP>
-__global__ void __launch_bounds__(kVecThreads) k_dense_vec(StreamDesc p, int64_t chunk, int want_presence,
+__global__ void __launch_bounds__(kVecThreads, 4) k_dense_vec(StreamDesc p, int64_t chunk, int want_presence,
                                                            size_t pres_off, size_t vec_off,
                                                            double* __restrict__ partials,
                                                            uint32_t* __restrict__ pres_partials) {
@@ -194,6 +194,7 @@ int dense_vec_grid(const StreamDesc& p, int want_presence) {
     DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p));
     const size_t smem = dense_vec_smem(p, want_presence);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kVecThreads, smem);
     per_sm = std::max(1, std::min(per_sm, p.ctas_per_sm > 0 ? p.ctas_per_sm : 4));
