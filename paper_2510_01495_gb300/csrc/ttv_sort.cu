@@ -729,7 +729,7 @@ struct RbkEmitSmem {
     RbkScanSmem ss;
 };
 
-__global__ void __launch_bounds__(kRbkThreads, 3) k_rbk_emit(const uint64_t* __restrict__ keys,
+__global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(const uint64_t* __restrict__ keys,
                                                              const double* __restrict__ vals, int64_t n,
                                                              const RbkSum* __restrict__ ingroup,
                                                              const RbkSum* __restrict__ gprefix,
