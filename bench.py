@@ -199,7 +199,14 @@ def run_reference(args, rank, world):
     t = problem.tensor
     subs, vals = t.subs.numpy(), t.vals.numpy()
     vecs = [v.numpy() for v in problem.vecs]
-    m = min(t.nnz, args.ref_sample)
+    # per-step sample: the oracle's measured rate on a calibration call sets
+    # it so that the whole --steps/--warmup run takes about ref_budget seconds
+    mc = min(t.nnz, 200_000)
+    t0 = time.perf_counter()
+    oracle.ttv(subs[:mc], vals[:mc], t.shape, problem.modes, vecs, dense=problem.dense)
+    rate = mc / max(time.perf_counter() - t0, 1e-6)
+    m = int(rate * args.ref_budget / max(1, args.steps + args.warmup))
+    m = max(1000, min(t.nnz, args.ref_sample, m))
     for _ in range(args.warmup):
         oracle.ttv(subs[:m], vals[:m], t.shape, problem.modes, vecs, dense=problem.dense)
     times = []
@@ -234,7 +241,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--nnz", type=int, default=None, help="smaller case of the workload (profiling)")
     ap.add_argument("--no-tune", action="store_true", help="batch_512: skip the autotuner (planner rule only)")
-    ap.add_argument("--ref-sample", type=int, default=1_000_000)
+    ap.add_argument("--ref-sample", type=int, default=1_000_000, help="largest per-step oracle sample")
+    ap.add_argument("--ref-budget", type=float, default=90.0, help="seconds the reference arm's timed steps aim at")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--scale", type=float, default=1.0, help="nnz scale for batch_512 / serve_64")
