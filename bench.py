@@ -188,6 +188,51 @@ def cpu_oracle_sample(problem, target_s: float = 10.0, max_nnz: int = 20_000_000
     return m2 / dt2 / 1e9, m2, dt2
 
 
+# ---- ranks: independent replicas (no data-path collective) -------------------
+
+def replica_seed(base: int, rank: int) -> int:
+    """Each rank draws its own replica of the workload."""
+    return base + 1000 * rank
+
+
+def init_ranks(world: int, dev):
+    """Process group for the barrier and the timing reduction (NCCL on the
+    GPU); None with one rank."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        if dev is not None and dev.type == "cuda":
+            dist.init_process_group("nccl", device_id=dev)
+        else:
+            dist.init_process_group("gloo")
+    return dist
+
+
+def sum_over_ranks(dist, value: float, dev) -> float:
+    """The sum of every rank's value (work done by all replicas)."""
+    if dist is None:
+        return value
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value: float, dev) -> float:
+    """The largest of every rank's value (timings: the slowest replica sets
+    the job's time)."""
+    if dist is None:
+        return value
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank, world):
     """The oracle, as it stands, on the host cores: each step a bounded sample."""
     if rank != 0:
@@ -266,15 +311,12 @@ def main():
     import paper_2510_01495_gb300 as ttv
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+    dist = init_ranks(world, dev)
     lib = ttv.load()
 
     wl = WORKLOADS[args.workload]
     # independent replica per rank: its own seed, no data-path collective
-    problem = wl["make"](dev, args.seed + 1000 * rank, args.nnz)
+    problem = wl["make"](dev, replica_seed(args.seed, rank), args.nnz)
     t = problem.tensor
     if args.layout == "soa":
         subs = t.subs.t().contiguous().t()
@@ -335,8 +377,7 @@ def main():
     time.sleep(0.3)
     ttv.profile_reset()
     ttv.profile_enable(True)
-    if dist:
-        dist.barrier()
+    barrier(dist)
     torch.cuda.synchronize(dev)
     launches0 = ttv.launch_count()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -351,17 +392,13 @@ def main():
     ev1.record(stream)
     nnz_out = finish(pending)
     torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
+    barrier(dist)
     launches = ttv.launch_count() - launches0
     ms = ev0.elapsed_time(ev1)
     ttv.profile_collect()
     ttv.profile_enable(False)
     clk = clocks.stop()
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(dist, ms, dev)
     nnz = problem.tensor.nnz
     value = nnz * args.steps * world / (ms * 1e-3) / 1e9
     ms_step = ms / args.steps
@@ -410,6 +447,10 @@ def main():
     # ---- end to end: host buffers through the public call ----
     if rank == 0 or world > 1:
         e2e = run_e2e(ttv, problem, subs, vals, vecs, fmt, args, dev)
+        if dist:
+            # whole job: every replica's nonzeros over the slowest replica's time
+            e2e["ms_per_step"] = max_over_ranks(dist, e2e["ms_per_step"], dev)
+            e2e["value"] = nnz * world / (e2e["ms_per_step"] * 1e-3) / 1e9
         line["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, m, dt = cpu_oracle_sample(problem)
@@ -435,7 +476,8 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     ttv.load()
-    probs = S.batch_problems(seed=args.seed + 1000 * rank, count=512, scale=args.scale, device=dev)
+    dist = init_ranks(world, dev)
+    probs = S.batch_problems(seed=replica_seed(args.seed, rank), count=512, scale=args.scale, device=dev)
     items = []
     for p in probs:
         t = p.tensor
@@ -467,12 +509,15 @@ def run_batch(args, rank, world, local_rank):
     ttv.profile_enable(False)
     l0 = ttv.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    torch.cuda.synchronize(dev)
     ev0.record(stream)
     for _ in range(args.steps):
         b.run()
     ev1.record(stream)
     torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1) / args.steps
+    barrier(dist)
+    ms = max_over_ranks(dist, ev0.elapsed_time(ev1) / args.steps, dev)
     launches = ttv.launch_count() - l0
     clk = clocks.stop()
     # the plain form: one launch sequence per problem, same buffers
@@ -508,6 +553,8 @@ def run_batch(args, rank, world, local_rank):
         "graph_kernel_launches_per_step": b.graph_launches(), "gpu_launches": launches, "clocks": clk,
         "autotune": {"classes_tuned": tuned, "seconds": round(t_tune, 2), "problems_by_path": chosen},
     }
+    if dist:
+        dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -521,11 +568,13 @@ def run_serve(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     ttv.load()
-    g = np.random.default_rng(args.seed + rank)
+    dist = init_ranks(world, dev)
+    seed = replica_seed(args.seed, rank)
+    g = np.random.default_rng(seed)
     tensors = []
     acc_sample = []   # FP64 originals of a few small tensors, for the accuracy report
     for i in range(64):
-        s = args.seed * 1000 + i
+        s = seed * 1000 + i
         r = S.uniform(s, 9, 2).numpy()
         nnz = max(1000, int(math.exp(math.log(1e4) + r[0] * (math.log(5e7) - math.log(1e4))) * args.scale))
         shp = None
@@ -558,6 +607,7 @@ def run_serve(args, rank, world, local_rank):
     clocks = _clock_start(local_rank)
     arrivals = np.cumsum(g.exponential(1.0 / args.rate, size=args.requests))
     rids = []
+    barrier(dist)
     t0 = time.perf_counter()
     for k, (ti, m, x) in enumerate(reqs[64:]):
         delay = arrivals[k] - (time.perf_counter() - t0)
@@ -567,9 +617,11 @@ def run_serve(args, rank, world, local_rank):
     for r in rids:
         srv.wait(r)
     wall = time.perf_counter() - t0
+    barrier(dist)
+    wall = max_over_ranks(dist, wall, dev)
     st = srv.stats()
     clk = clocks.stop()
-    served_nnz = sum(nnzs[ti] for ti, _, _ in reqs[64:])
+    served_nnz = sum_over_ranks(dist, sum(nnzs[ti] for ti, _, _ in reqs[64:]), dev)
     n_plain = min(300, args.requests)
     plain.reset_stats()
     t1 = time.perf_counter()
@@ -610,12 +662,14 @@ def run_serve(args, rank, world, local_rank):
                    "requests": args.requests, "scale": args.scale, "resident_bytes": resident, "slots": 8,
                    "budget_bytes": 60 << 30},
         "serve": {"p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
-                  "throughput_rps": args.requests / wall, "completed": st["completed"]},
+                  "throughput_rps": args.requests * world / wall, "completed": st["completed"]},
         "plain": {"requests": n_plain, "throughput_rps": n_plain / wall_plain,
                   "throughput_gnnz_s": plain_nnz / wall_plain / 1e9, "p50_ms": pst["p50_us"] / 1e3,
                   "p99_ms": pst["p99_us"] / 1e3},
         "clocks": clk, "accuracy_fp32_storage": accuracy,
     }
+    if dist:
+        dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
