@@ -213,15 +213,18 @@ void ttv_batch_release(void);
  * value and vector dtypes, subscript layout, ceil(log2 nnz), ceil(log2 of
  * the key space prod shape[R])).  ttv_autotune runs every applicable
  * candidate on the given problem -- accumulation path (DENSE, SORT, HASH,
- * BUCKET) x CTAs per SM of the streaming pass (1-4 for DENSE, 4/8/16 for SORT
- * and HASH) -- `trials` times after one warm-up run each, takes the median
- * of CUDA-event times on `stream`, and records the fastest for the class.
+ * BUCKET) x CTAs per SM of the streaming pass (2/3/4 for DENSE, 4/8/16 for
+ * SORT, 8/16 for HASH) x nonzeros per thread per iteration (DENSE: 1 or 2
+ * pairs; HASH: 2 or 4) -- `trials` times after one warm-up run each, takes
+ * the median of CUDA-event times on `stream`, and records the fastest for
+ * the class.
  * Every later call with path AUTO, fp64 accumulation and no determinism
  * request (ttv_multi, ttv_batch, the server) whose problem falls in a
  * recorded class uses the recorded plan; other calls are unaffected.  The
  * record lives in host memory, shared by all threads; ttv_tune_save /
- * ttv_tune_load keep it in a text file ("ttv-tune 1" header, then one
- * "<class hex> <path> <ctas_per_sm> <ms>" line per class; loading merges).
+ * ttv_tune_load keep it in a text file ("ttv-tune 2" header, then one
+ * "<class hex> <path> <ctas_per_sm> <items_per_thread> <ms>" line per class;
+ * loading merges).
  * ttv_autotune synchronises `stream` once per trial and allocates its own
  * workspace and results; it returns TTV_ERR_ARG for deterministic or
  * non-fp64 options and TTV_ERR_UNSUPPORTED when no candidate can run (an
@@ -230,10 +233,12 @@ void ttv_batch_release(void);
 typedef struct {
     int32_t path;                /* chosen ttv_path                                */
     int32_t ctas_per_sm;         /* chosen CTAs per SM of the streaming pass        */
+    int32_t items_per_thread;    /* chosen nonzeros per thread (0: path default)    */
     double ms;                   /* its median time                                */
     int32_t n_candidates;        /* candidates that ran                             */
     int32_t cand_path[TTV_TUNE_MAX_CANDIDATES];
     int32_t cand_ctas[TTV_TUNE_MAX_CANDIDATES];
+    int32_t cand_items[TTV_TUNE_MAX_CANDIDATES];
     double cand_ms[TTV_TUNE_MAX_CANDIDATES];
 } ttv_tune_result;
 
@@ -247,9 +252,9 @@ void ttv_tune_clear(void);
 int ttv_tune_count(void);                /* recorded classes */
 /* 1 and the recorded plan if the problem's class (vectors taken as FP64 for
  * the class key) has a record, 0 if not, a negative error code for an
- * invalid problem.  path / ctas_per_sm may be NULL. */
+ * invalid problem.  path / ctas_per_sm / items_per_thread may be NULL. */
 int ttv_tune_lookup(const ttv_tensor *t, const int32_t *modes, int32_t n_v, const ttv_opts *opts, int32_t *path,
-                    int32_t *ctas_per_sm);
+                    int32_t *ctas_per_sm, int32_t *items_per_thread);
 
 /* ---- serving ------------------------------------------------------------------
  * A continuous-batching TTV server.  Registered tensors stay resident in

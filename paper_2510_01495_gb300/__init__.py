@@ -319,9 +319,10 @@ PATH_NAME = {v: k for k, v in PATH.items()}
 
 
 class TuneResult(ctypes.Structure):
-    _fields_ = [("path", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("ms", ctypes.c_double),
-                ("n_candidates", ctypes.c_int32), ("cand_path", ctypes.c_int32 * TUNE_MAX),
-                ("cand_ctas", ctypes.c_int32 * TUNE_MAX), ("cand_ms", ctypes.c_double * TUNE_MAX)]
+    _fields_ = [("path", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("items_per_thread", ctypes.c_int32),
+                ("ms", ctypes.c_double), ("n_candidates", ctypes.c_int32), ("cand_path", ctypes.c_int32 * TUNE_MAX),
+                ("cand_ctas", ctypes.c_int32 * TUNE_MAX), ("cand_items", ctypes.c_int32 * TUNE_MAX),
+                ("cand_ms", ctypes.c_double * TUNE_MAX)]
 
 
 def _declare_tune(lib):
@@ -340,7 +341,7 @@ def _declare_tune(lib):
     lib.ttv_tune_count.argtypes = []
     lib.ttv_tune_count.restype = ctypes.c_int
     lib.ttv_tune_lookup.argtypes = [P(Tensor), P(ctypes.c_int32), ctypes.c_int32, P(Opts), P(ctypes.c_int32),
-                                    P(ctypes.c_int32)]
+                                    P(ctypes.c_int32), P(ctypes.c_int32)]
     lib.ttv_tune_lookup.restype = ctypes.c_int
     lib._tune_declared = True
     return lib
@@ -358,22 +359,25 @@ def autotune(subs, vals, shape, modes, vecs, *, fmt="sparse", trials=5, determin
     r = TuneResult()
     _check(lib, lib.ttv_autotune(ctypes.byref(t), m, len(modes), vp, DTYPE[vdt], ctypes.byref(o), int(trials),
                                  ctypes.byref(r), _stream_handle(stream)))
-    cands = [{"path": PATH_NAME[r.cand_path[i]], "ctas_per_sm": r.cand_ctas[i], "ms": r.cand_ms[i]}
-             for i in range(r.n_candidates)]
-    return {"path": PATH_NAME[r.path], "ctas_per_sm": r.ctas_per_sm, "ms": r.ms, "candidates": cands}
+    cands = [{"path": PATH_NAME[r.cand_path[i]], "ctas_per_sm": r.cand_ctas[i], "items_per_thread": r.cand_items[i],
+              "ms": r.cand_ms[i]} for i in range(r.n_candidates)]
+    return {"path": PATH_NAME[r.path], "ctas_per_sm": r.ctas_per_sm, "items_per_thread": r.items_per_thread,
+            "ms": r.ms, "candidates": cands}
 
 
 def tune_lookup(subs, vals, shape, modes, *, fmt="sparse"):
-    """(path name, CTAs per SM) recorded for this problem's class, or None."""
+    """(path name, CTAs per SM, items per thread) recorded for this problem's
+    class, or None."""
     lib = _declare_tune(load())
     t = make_tensor(subs, vals, shape)
     m = (ctypes.c_int32 * len(modes))(*[int(x) for x in modes])
     o = make_opts(fmt=fmt)
-    pth, ctas = ctypes.c_int32(), ctypes.c_int32()
-    rc = lib.ttv_tune_lookup(ctypes.byref(t), m, len(modes), ctypes.byref(o), ctypes.byref(pth), ctypes.byref(ctas))
+    pth, ctas, items = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    rc = lib.ttv_tune_lookup(ctypes.byref(t), m, len(modes), ctypes.byref(o), ctypes.byref(pth), ctypes.byref(ctas),
+                             ctypes.byref(items))
     if rc < 0:
         _check(lib, rc)
-    return (PATH_NAME[pth.value], ctas.value) if rc == 1 else None
+    return (PATH_NAME[pth.value], ctas.value, items.value) if rc == 1 else None
 
 
 def tune_save(path: str):

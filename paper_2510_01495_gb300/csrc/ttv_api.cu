@@ -170,12 +170,14 @@ static int bits_for(uint64_t nkeys) {
 struct TuneRec {
     int32_t path;
     int32_t ctas;
+    int32_t items;
     double ms;
 };
 static std::mutex g_tune_mu;
 static std::vector<std::pair<uint64_t, TuneRec>> g_tune;
 static thread_local int t_force_path = -1;   // set by the autotuner's trial runs
 static thread_local int t_force_ctas = 0;
+static thread_local int t_force_items = 0;
 
 static uint64_t tune_key(const StreamDesc& p, int dense_out) {
     const uint64_t layout = p.snz == 1 ? 1 : (p.smode == 1 ? 0 : 2);
@@ -273,14 +275,17 @@ static int make_plan(const ttv_tensor* t, const int32_t* modes, int32_t n_v, con
     const bool dense_ok = (int64_t)p.nkeys <= kDenseMaxCells;
     const bool want_exact = o->accum == TTV_ACCUM_EXACT || o->deterministic;
     p.ctas_per_sm = 0;
+    p.items = 0;
     if (t_force_path >= 0) {
         path = t_force_path;
         p.ctas_per_sm = t_force_ctas;
+        p.items = t_force_items;
     } else if (path == TTV_PATH_AUTO && !want_exact && !pl.compensated) {
         TuneRec r;
         if (tune_lookup(tune_key(p, pl.dense_out), r) && (r.path != TTV_PATH_DENSE || dense_ok || pl.order0)) {
             path = r.path;
             p.ctas_per_sm = r.ctas;
+            p.items = r.items;
         }
     }
     if (path == TTV_PATH_AUTO) {
@@ -697,16 +702,20 @@ int ttv_autotune(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const v
     const StreamDesc& p = base.desc;
     const uint64_t key = tune_key(p, base.dense_out);
 
-    struct Cand { int path, ctas; };
+    // candidates: path x CTAs per SM of the streaming pass x nonzeros per
+    // thread (DENSE: 1 or 2 pairs per iteration; HASH: 2 or 4 per iteration)
+    struct Cand { int path, ctas, items; };
     std::vector<Cand> cands;
     const bool dense_ok = (int64_t)p.nkeys <= kDenseMaxCells || base.order0;
     if (dense_ok)
-        for (int c = 1; c <= 4; ++c) cands.push_back({TTV_PATH_DENSE, c});
+        for (int it : {1, 2})
+            for (int c : {2, 3, 4}) cands.push_back({TTV_PATH_DENSE, c, it});
     if (!base.order0 && p.nnz > 0 && p.nnz <= kMaxSortN) {
-        for (int c : {4, 8, 16}) cands.push_back({TTV_PATH_SORT, c});
+        for (int c : {4, 8, 16}) cands.push_back({TTV_PATH_SORT, c, 0});
         if (hash_applicable(p))
-            for (int c : {4, 8, 16}) cands.push_back({TTV_PATH_HASH, c});
-        if (!base.dense_out && bucket_applicable(p)) cands.push_back({TTV_PATH_BUCKET, 0});
+            for (int it : {4, 2})
+                for (int c : {8, 16}) cands.push_back({TTV_PATH_HASH, c, it});
+        if (!base.dense_out && bucket_applicable(p)) cands.push_back({TTV_PATH_BUCKET, 0, 0});
     }
 
     cudaEvent_t e0, e1;
@@ -717,10 +726,12 @@ int ttv_autotune(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const v
         if (res->n_candidates >= TTV_TUNE_MAX_CANDIDATES) break;
         t_force_path = c.path;
         t_force_ctas = c.ctas;
+        t_force_items = c.items;
         Plan pl;
         rc = make_plan(t, modes, n_v, vecs, v_dtype, nullptr, &o, pl);
         t_force_path = -1;
         t_force_ctas = 0;
+        t_force_items = 0;
         if (rc != TTV_OK || pl.path != c.path) continue;
         std::vector<float> times;
         bool ok = true;
@@ -743,6 +754,7 @@ int ttv_autotune(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const v
         const int i = res->n_candidates++;
         res->cand_path[i] = c.path;
         res->cand_ctas[i] = c.ctas;
+        res->cand_items[i] = c.items;
         res->cand_ms[i] = med;
         if (best < 0 || med < res->cand_ms[best]) best = i;
     }
@@ -752,8 +764,9 @@ int ttv_autotune(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const v
     if (best < 0) return fail(TTV_ERR_UNSUPPORTED, "no candidate plan ran (empty tensor or no applicable path)");
     res->path = res->cand_path[best];
     res->ctas_per_sm = res->cand_ctas[best];
+    res->items_per_thread = res->cand_items[best];
     res->ms = res->cand_ms[best];
-    tune_record(key, TuneRec{res->path, res->ctas_per_sm, res->ms});
+    tune_record(key, TuneRec{res->path, res->ctas_per_sm, res->items_per_thread, res->ms});
     return TTV_OK;
 }
 
@@ -763,9 +776,10 @@ int ttv_tune_save(const char* path) {
     FILE* f = fopen(path, "w");
     if (!f) return fail(TTV_ERR_ARG, "cannot open %s for writing", path);
     std::lock_guard<std::mutex> g(g_tune_mu);
-    fprintf(f, "ttv-tune 1\n");
+    fprintf(f, "ttv-tune 2\n");
     for (auto& e : g_tune)
-        fprintf(f, "%016llx %d %d %.6f\n", (unsigned long long)e.first, e.second.path, e.second.ctas, e.second.ms);
+        fprintf(f, "%016llx %d %d %d %.6f\n", (unsigned long long)e.first, e.second.path, e.second.ctas,
+                e.second.items, e.second.ms);
     const bool bad = ferror(f) != 0;
     fclose(f);
     return bad ? fail(TTV_ERR_ARG, "write to %s failed", path) : TTV_OK;
@@ -778,16 +792,17 @@ int ttv_tune_load(const char* path) {
     if (!f) return fail(TTV_ERR_ARG, "cannot open %s", path);
     char head[32] = {0};
     int version = 0;
-    if (fscanf(f, "%31s %d", head, &version) != 2 || strcmp(head, "ttv-tune") != 0 || version != 1) {
+    if (fscanf(f, "%31s %d", head, &version) != 2 || strcmp(head, "ttv-tune") != 0 || version != 2) {
         fclose(f);
-        return fail(TTV_ERR_ARG, "%s is not a version-1 tuning file", path);
+        return fail(TTV_ERR_ARG, "%s is not a version-2 tuning file", path);
     }
     std::vector<std::pair<uint64_t, TuneRec>> recs;
     unsigned long long k;
     TuneRec r;
     int n;
-    while ((n = fscanf(f, "%llx %d %d %lf", &k, &r.path, &r.ctas, &r.ms)) == 4) {
-        if (r.path < TTV_PATH_DENSE || r.path > TTV_PATH_BUCKET || r.ctas < 0 || r.ctas > 64) {
+    while ((n = fscanf(f, "%llx %d %d %d %lf", &k, &r.path, &r.ctas, &r.items, &r.ms)) == 5) {
+        if (r.path < TTV_PATH_DENSE || r.path > TTV_PATH_BUCKET || r.ctas < 0 || r.ctas > 64 || r.items < 0 ||
+            r.items > 16) {
             fclose(f);
             return fail(TTV_ERR_ARG, "bad record in %s", path);
         }
@@ -801,7 +816,7 @@ int ttv_tune_load(const char* path) {
 }
 
 int ttv_tune_lookup(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const ttv_opts* opts, int32_t* path,
-                    int32_t* ctas_per_sm) {
+                    int32_t* ctas_per_sm, int32_t* items_per_thread) {
     g_err.clear();
     ttv_opts o;
     if (opts) o = *opts;
@@ -816,6 +831,7 @@ int ttv_tune_lookup(const ttv_tensor* t, const int32_t* modes, int32_t n_v, cons
     if (!tune_lookup(tune_key(pl.desc, pl.dense_out), r)) return 0;
     if (path) *path = r.path;
     if (ctas_per_sm) *ctas_per_sm = r.ctas;
+    if (items_per_thread) *items_per_thread = r.items;
     return 1;
 }
 

@@ -16,7 +16,9 @@
 namespace ttv {
 
 constexpr int kVecThreads = 256;
-constexpr int kVecPairs = 1;       // pairs of nonzeros per thread per iteration (59 registers: 4 CTAs per SM)
+// Pairs of nonzeros per thread per iteration: 1 (59 registers, 4 CTAs per
+// SM; the default) or 2 (more loads in flight per thread, 3 CTAs per SM);
+// the autotuner picks per problem class.
 
 template <int D, bool kIntP>
 __device__ __forceinline__ void dense_item(const StreamDesc& p, const double* sv, const SigEntry* sve,
@@ -61,8 +63,8 @@ __device__ __forceinline__ void dense_item(const StreamDesc& p, const double* sv
     if (want_presence) atomicOr(&pres[key >> 5], 1u << (key & 31));
 }
 
-template <int D, bool kSoA, bool kIntP>
-__global__ void __launch_bounds__(kVecThreads, 4) k_dense_vec(StreamDesc p, int64_t chunk, int want_presence,
+template <int D, bool kSoA, bool kIntP, int kVecPairs>
+__global__ void __launch_bounds__(kVecThreads, kVecPairs == 1 ? 4 : 3) k_dense_vec(StreamDesc p, int64_t chunk, int want_presence,
                                                            size_t pres_off, size_t vec_off,
                                                            double* __restrict__ partials,
                                                            uint32_t* __restrict__ pres_partials) {
@@ -151,19 +153,26 @@ __global__ void __launch_bounds__(kVecThreads, 4) k_dense_vec(StreamDesc p, int6
 // ---- host side ------------------------------------------------------------
 typedef void (*DenseVecKernel)(StreamDesc, int64_t, int, size_t, size_t, double*, uint32_t*);
 
-template <int D>
-static DenseVecKernel pick(bool soa, bool intp) {
-    if (soa) return intp ? k_dense_vec<D, true, true> : k_dense_vec<D, true, false>;
-    return intp ? k_dense_vec<D, false, true> : k_dense_vec<D, false, false>;
+template <int D, int P>
+static DenseVecKernel pick_p(bool soa, bool intp) {
+    if (soa) return intp ? k_dense_vec<D, true, true, P> : k_dense_vec<D, true, false, P>;
+    return intp ? k_dense_vec<D, false, true, P> : k_dense_vec<D, false, false, P>;
 }
 
-static DenseVecKernel dense_vec_kernel(int d, bool soa, bool intp) {
+template <int D>
+static DenseVecKernel pick(bool soa, bool intp, int pairs) {
+    return pairs == 2 ? pick_p<D, 2>(soa, intp) : pick_p<D, 1>(soa, intp);
+}
+
+static int dense_vec_pairs(const StreamDesc& p) { return p.items == 2 ? 2 : 1; }
+
+static DenseVecKernel dense_vec_kernel(int d, bool soa, bool intp, int pairs) {
     switch (d) {
-        case 2: return pick<2>(soa, intp);
-        case 3: return pick<3>(soa, intp);
-        case 4: return pick<4>(soa, intp);
-        case 5: return pick<5>(soa, intp);
-        case 6: return pick<6>(soa, intp);
+        case 2: return pick<2>(soa, intp, pairs);
+        case 3: return pick<3>(soa, intp, pairs);
+        case 4: return pick<4>(soa, intp, pairs);
+        case 5: return pick<5>(soa, intp, pairs);
+        case 6: return pick<6>(soa, intp, pairs);
         default: return nullptr;
     }
 }
@@ -191,14 +200,14 @@ size_t dense_vec_smem(const StreamDesc& p, int want_presence) {
 
 int dense_vec_grid(const StreamDesc& p, int want_presence) {
     const bool soa = p.snz == 1;
-    DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p));
+    DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p), dense_vec_pairs(p));
     const size_t smem = dense_vec_smem(p, want_presence);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kVecThreads, smem);
     per_sm = std::max(1, std::min(per_sm, p.ctas_per_sm > 0 ? p.ctas_per_sm : 4));
-    const int64_t min_chunk = std::max<int64_t>((int64_t)kVecThreads * kVecPairs * 2 * 4, (int64_t)p.nkeys * 4);
+    const int64_t min_chunk = std::max<int64_t>((int64_t)kVecThreads * dense_vec_pairs(p) * 2 * 4, (int64_t)p.nkeys * 4);
     const int64_t by_work = std::max<int64_t>(1, (p.nnz + min_chunk - 1) / min_chunk);
     return (int)std::max<int64_t>(1, std::min<int64_t>(by_work, (int64_t)num_sms() * per_sm));
 }
@@ -206,7 +215,7 @@ int dense_vec_grid(const StreamDesc& p, int want_presence) {
 void launch_dense_vec(const StreamDesc& p, int want_presence, int G, double* partials, uint32_t* pres_partials,
                       cudaStream_t stream) {
     const bool soa = p.snz == 1;
-    DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p));
+    DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p), dense_vec_pairs(p));
     const size_t smem = dense_vec_smem(p, want_presence);
     size_t pres_off = (size_t)p.nkeys * sizeof(double);
     size_t vec_off = pres_off + (want_presence ? ((p.nkeys + 31) / 32) * sizeof(uint32_t) : 0);

@@ -35,7 +35,10 @@ namespace ttv {
 
 constexpr unsigned long long kHashEmpty = ~0ull;   // keys are < nkeys <= 2^64 - 1
 constexpr int kHashThreads = 256;
-constexpr int kHashUnroll = 4;
+// nonzeros per thread per iteration of the insert: 2 (default: measured
+// faster than 4 on every class tried, the insert being bound by L2 atomics
+// rather than by loads in flight) or 4, picked per problem class by the
+// autotuner
 constexpr int kHashTileShift = 12;                 // entries per count tile: 4096
 constexpr int kHashTile = 1 << kHashTileShift;
 constexpr int kHashItems = kHashTile / kHashThreads;
@@ -183,7 +186,7 @@ __device__ __noinline__ void hash_probe_on(uint64_t key, double t, uint64_t h0, 
 // possible: direct = presence OR (skipped when the bit reads set) + binary64
 // add; hashed = compare-and-swap + binary64 add.  Entries are counted
 // afterwards, not here.
-template <bool kDirect>
+template <bool kDirect, int kHashUnroll>
 __global__ void __launch_bounds__(kHashThreads) k_hash_insert(StreamDesc p, HashSlot* slots, double* dvals,
                                                               uint32_t* bits, int log2cap, uint32_t* tile_count) {
     extern __shared__ double sv[];
@@ -453,9 +456,11 @@ void launch_hash(const StreamDesc& p, int dense_out, int key_bits, void* ws, int
 
     // insert
     const size_t smem = p.vec_smem ? (size_t)p.vtotal * sizeof(double) : 0;
-    auto kins = h.direct ? k_hash_insert<true> : k_hash_insert<false>;
+    const int unroll = p.items == 4 ? 4 : 2;
+    auto kins = h.direct ? (unroll == 2 ? k_hash_insert<true, 2> : k_hash_insert<true, 4>)
+                         : (unroll == 2 ? k_hash_insert<false, 2> : k_hash_insert<false, 4>);
     if (smem > 48 * 1024) cudaFuncSetAttribute(kins, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int64_t want = (p.nnz + kHashThreads * kHashUnroll - 1) / (kHashThreads * kHashUnroll);
+    const int64_t want = (p.nnz + kHashThreads * unroll - 1) / (kHashThreads * unroll);
     const int per_sm = p.ctas_per_sm > 0 ? p.ctas_per_sm : 8;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * per_sm));
     TTV_LAUNCH("hash_insert", stream, kins<<<grid, kHashThreads, smem, stream>>>(p, w.slots, acc, w.bits, h.log2cap, w.tile_count));

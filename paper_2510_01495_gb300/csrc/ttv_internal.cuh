@@ -57,6 +57,7 @@ struct StreamDesc {
     uint64_t rmagic[kMaxD];           // division by rshape[j] (see udiv_invariant)
     uint32_t rsh[kMaxD];              // shift pair: sh1 | sh2 << 8
     int32_t ctas_per_sm;              // grid of the streaming pass: CTAs per SM (0: default)
+    int32_t items;                    // nonzeros (dense: pairs) per thread per iteration (0: default)
     Status* status;
 };
 
