@@ -256,6 +256,38 @@ int ttv_tune_count(void);                /* recorded classes */
 int ttv_tune_lookup(const ttv_tensor *t, const int32_t *modes, int32_t n_v, const ttv_opts *opts, int32_t *path,
                     int32_t *ctas_per_sm, int32_t *items_per_thread);
 
+/* ---- prepared tensors ----------------------------------------------------------
+ * For repeated TTVs of one resident tensor along one fixed set of modes S
+ * with fresh vectors.  The grouping of Sec. 3.3 (one result row per distinct
+ * surviving tuple, ascending) depends on the tensor only, so ttv_prepare
+ * sorts the nonzeros once by their surviving key (stable: equal keys keep
+ * input order) and keeps, in that order, the keys (8 bytes per nonzero), the
+ * values (val_dtype) and the subscripts of the modes in S (int32; every mode
+ * in S must be smaller than 2^31).  ttv_prepared_run is then one streaming
+ * reduce-by-key over those arrays with the terms vals * prod x_m[sub_m]
+ * formed on the fly in increasing mode order: its result equals, bit for bit,
+ * that of ttv_multi with path SORT and fp64 accumulation on the same inputs.
+ *
+ * ttv_prepare copies what it needs (the caller's arrays may be freed
+ * afterwards) into device memory owned by the handle (ttv_prepared_info
+ * reports the bytes), synchronises `stream` once and returns
+ * TTV_ERR_SUBSCRIPT / TTV_ERR_MODE / TTV_ERR_KEY_OVERFLOW / TTV_ERR_ARG like
+ * ttv_multi, TTV_ERR_UNSUPPORTED for nnz >= 2^30 or a contracted mode of
+ * 2^31 or more entries.  ttv_prepared_run takes the vectors in the order of
+ * the modes given to ttv_prepare (vec_lens may be NULL; else each must equal
+ * its mode size), opts as ttv_multi (fmt, workspace, async; accum must be
+ * TTV_ACCUM_FP64, path is ignored), and fills `out` like ttv_multi: for a
+ * sparse result nnz_out rows (ttv_prepared_info), for a dense one
+ * prod(shape[R]) values.  Runs on one handle may overlap on different
+ * streams; ttv_prepared_free synchronises the device and releases it. */
+typedef struct ttv_prepared ttv_prepared;
+int ttv_prepare(const ttv_tensor *t, const int32_t *modes, int32_t n_v, ttv_prepared **out, ttv_stream_t stream);
+int ttv_prepared_run(const ttv_prepared *p, const void *const *vecs, const int64_t *vec_lens, ttv_dtype v_dtype,
+                     ttv_out *out, const ttv_opts *opts, ttv_stream_t stream);
+int ttv_prepared_info(const ttv_prepared *p, int64_t *nnz_out, int32_t *order, size_t *device_bytes);
+int ttv_prepared_workspace_size(const ttv_prepared *p, size_t *bytes);
+void ttv_prepared_free(ttv_prepared *p);
+
 /* ---- serving ------------------------------------------------------------------
  * A continuous-batching TTV server.  Registered tensors stay resident in
  * server-owned device memory.  Requests (contracted modes + host vectors)

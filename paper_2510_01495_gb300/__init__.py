@@ -312,6 +312,106 @@ def profile_names():
     return [x for x in buf.value.decode().split("\n") if x]
 
 
+# ---- prepared tensors -------------------------------------------------------------
+
+def _declare_prep(lib):
+    if getattr(lib, "_prep_declared", False):
+        return lib
+    P = ctypes.POINTER
+    lib.ttv_prepare.argtypes = [P(Tensor), P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_void_p), ctypes.c_void_p]
+    lib.ttv_prepare.restype = ctypes.c_int
+    lib.ttv_prepared_run.argtypes = [ctypes.c_void_p, P(ctypes.c_void_p), P(ctypes.c_int64), ctypes.c_int, P(Out),
+                                     P(Opts), ctypes.c_void_p]
+    lib.ttv_prepared_run.restype = ctypes.c_int
+    lib.ttv_prepared_info.argtypes = [ctypes.c_void_p, P(ctypes.c_int64), P(ctypes.c_int32), P(ctypes.c_size_t)]
+    lib.ttv_prepared_info.restype = ctypes.c_int
+    lib.ttv_prepared_workspace_size.argtypes = [ctypes.c_void_p, P(ctypes.c_size_t)]
+    lib.ttv_prepared_workspace_size.restype = ctypes.c_int
+    lib.ttv_prepared_free.argtypes = [ctypes.c_void_p]
+    lib.ttv_prepared_free.restype = None
+    lib._prep_declared = True
+    return lib
+
+
+class Prepared:
+    """A tensor prepared for repeated TTVs along ``modes`` (see ttv_prepare):
+    ``run(vecs)`` takes one vector per mode, in the order of ``modes``."""
+
+    def __init__(self, subs: torch.Tensor, vals: torch.Tensor, shape, modes, stream=None):
+        self._lib = _declare_prep(load())
+        self.modes = [int(m) for m in modes]
+        self.shape = tuple(int(x) for x in shape)
+        self.device = subs.device
+        t = make_tensor(subs, vals, shape)
+        m = (ctypes.c_int32 * len(self.modes))(*self.modes)
+        h = ctypes.c_void_p()
+        _check(self._lib, self._lib.ttv_prepare(ctypes.byref(t), m, len(self.modes), ctypes.byref(h),
+                                                _stream_handle(stream)))
+        self._h = h
+        nnz_out, order, nbytes = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_size_t()
+        _check(self._lib, self._lib.ttv_prepared_info(h, ctypes.byref(nnz_out), ctypes.byref(order),
+                                                      ctypes.byref(nbytes)))
+        self.nnz_out, self.order, self.device_bytes = int(nnz_out.value), int(order.value), int(nbytes.value)
+        ws = ctypes.c_size_t()
+        _check(self._lib, self._lib.ttv_prepared_workspace_size(h, ctypes.byref(ws)))
+        self.workspace_bytes = int(ws.value)
+
+    def run(self, vecs, *, fmt="sparse", out_subs=None, out_vals=None, workspace=None, stream=None) -> Result:
+        if self._h is None:
+            raise RuntimeError("prepared tensor released")
+        if len(vecs) != len(self.modes):
+            raise ValueError("one vector per prepared mode")
+        vdt = vecs[0].dtype
+        for v in vecs:
+            if not v.is_cuda or v.dtype != vdt or v.dim() != 1 or (v.numel() > 1 and v.stride(0) != 1):
+                raise ValueError("vectors must be contiguous CUDA vectors of one dtype")
+        if vdt not in DTYPE:
+            raise TypeError("vectors must be float64 or float32")
+        vp = (ctypes.c_void_p * len(vecs))(*[v.data_ptr() for v in vecs])
+        lens = (ctypes.c_int64 * len(vecs))(*[v.numel() for v in vecs])
+        surv = [self.shape[m] for m in range(len(self.shape)) if m not in self.modes]
+        dense = fmt == "dense" or not surv
+        ncells = 1
+        for x in surv:
+            ncells *= x
+        if workspace is None:
+            workspace = torch.empty(max(1, self.workspace_bytes), dtype=torch.uint8, device=self.device)
+        if out_vals is None:
+            out_vals = torch.empty(max(1, ncells if dense else self.nnz_out), dtype=torch.float64, device=self.device)
+        if out_subs is None and not dense:
+            out_subs = torch.empty((max(1, self.nnz_out), self.order), dtype=torch.int64, device=self.device)
+        o = make_opts(fmt=fmt, workspace=workspace)
+        res = Out()
+        res.vals = out_vals.data_ptr()
+        res.vals_capacity = out_vals.numel()
+        if out_subs is not None:
+            res.subs = out_subs.data_ptr()
+            res.subs_capacity = out_subs.shape[0]
+        try:
+            _check(self._lib, self._lib.ttv_prepared_run(self._h, vp, lens, DTYPE[vdt], ctypes.byref(res),
+                                                         ctypes.byref(o), _stream_handle(stream)))
+            newshape = tuple(int(res.shape[j]) for j in range(res.order))
+            n = int(res.nnz)
+            if res.is_dense:
+                return Result(None, out_vals[:n].view(newshape), newshape, True)
+            subs_out = out_subs[:n] if out_subs is not None else torch.zeros((n, 0), dtype=torch.int64,
+                                                                               device=self.device)
+            return Result(subs_out, out_vals[:n], newshape, False)
+        finally:
+            self._lib.ttv_out_free(ctypes.byref(res))
+
+    def close(self):
+        if self._h is not None:
+            self._lib.ttv_prepared_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---- autotuner ------------------------------------------------------------------
 
 TUNE_MAX = 16

@@ -33,6 +33,12 @@ void launch_seg_reduce(const uint64_t* keys, const double* vals, int64_t n, uint
                        unsigned long long* lookback, uint32_t* ticket, uint32_t* long_list, const StreamDesc& p,
                        const SegOut& o, Status* st, cudaStream_t stream);
 size_t rbk_state_bytes(int64_t n);
+void launch_reduce_by_key_prepared(const uint64_t* keys, const PrepTerms& terms, int64_t n, void* state,
+                                   const StreamDesc& p, const SegOut& o, Status* st, cudaStream_t stream);
+void launch_prep_keys(const StreamDesc& p, uint64_t* keys, double* idx, cudaStream_t stream);
+void launch_prep_gather(const StreamDesc& p, const double* idx_sorted, void* vals_out, const PrepTerms& subs,
+                        cudaStream_t stream);
+void launch_prep_count(const uint64_t* keys, int64_t n, unsigned long long* count, cudaStream_t stream);
 void launch_reduce_by_key(const uint64_t* keys, const double* vals, int64_t n, void* state, const StreamDesc& p,
                           const SegOut& o, Status* st, cudaStream_t stream);
 
@@ -549,6 +555,120 @@ static int execute(const Plan& pl, ttv_out* out, const ttv_opts* o, cudaStream_t
     return finalize(out);
 }
 
+// ---- prepared tensors ------------------------------------------------------
+
+}  // namespace ttv
+
+struct ttv_prepared {
+    ttv::Plan plan;                   // shape, surviving modes, key strides, delinearisation
+    int32_t n_v = 0;
+    int32_t arg_of[TTV_MAX_D] = {0};  // j-th contracted mode (increasing) -> caller's vector index
+    int64_t nnz = 0;
+    int64_t nnz_out = 0;              // distinct keys (result rows)
+    uint64_t* keys = nullptr;         // sorted keys
+    void* vals = nullptr;             // values in key order
+    int32_t* subs[TTV_MAX_D] = {nullptr};
+    size_t bytes = 0;
+};
+
+namespace ttv {
+
+static size_t prepared_ws_bytes(const ttv_prepared* h) {
+    Arena a;
+    a.take<Status>(1);
+    a.take<char>(rbk_state_bytes(h->nnz));
+    a.off = (a.off + 255) & ~size_t(255);
+    return a.off;
+}
+
+static int execute_prepared(const ttv_prepared* h, const void* const* vecs, ttv_dtype vd, ttv_out* out,
+                            const ttv_opts* o, cudaStream_t stream) {
+    const StreamDesc& p0 = h->plan.desc;
+    const bool order0 = h->plan.order0;
+    bool dense_out = o->fmt == TTV_OUT_DENSE || order0;
+    if (o->fmt == TTV_OUT_AUTO && (double)h->nnz_out > 0.5 * (double)p0.nkeys) dense_out = true;
+    if (dense_out && !order0 && (double)p0.nkeys * 8.0 > 64e9)
+        return fail(TTV_ERR_UNSUPPORTED, "dense result of %llu cells", (unsigned long long)p0.nkeys);
+    if (out->internal) return fail(TTV_ERR_ARG, "ttv_out reused without ttv_out_free");
+    OutState* st = new OutState();
+    st->stream = stream;
+    st->dense_out = dense_out;
+    out->internal = st;
+    out->order = p0.nr;
+    for (int j = 0; j < TTV_MAX_D; ++j) out->shape[j] = j < p0.nr ? p0.rshape[j] : 0;
+    out->dtype = TTV_F64;
+    out->is_dense = dense_out && !order0;
+    out->nnz = dense_out ? (int64_t)p0.nkeys : 0;
+    st->hstatus = g_status_pool.acquire();
+    if (!st->hstatus) return fail(TTV_ERR_NOMEM, "pinned status allocation failed");
+    memset(st->hstatus, 0, sizeof(Status));
+    const int64_t cap_vals = dense_out ? (int64_t)p0.nkeys : h->nnz_out;
+    cudaError_t e;
+    if (!out->vals) {
+        e = cudaMallocAsync(&out->vals, (size_t)std::max<int64_t>(cap_vals, 1) * sizeof(double), stream);
+        if (e != cudaSuccess) { out->vals = nullptr; return cuda_fail(e, "output allocation"); }
+        st->owned_vals = out->vals;
+        out->vals_capacity = cap_vals;
+        if (!dense_out && p0.nr > 0) {
+            e = cudaMallocAsync((void**)&out->subs, (size_t)std::max<int64_t>(h->nnz_out, 1) * p0.nr * sizeof(int64_t),
+                                stream);
+            if (e != cudaSuccess) { out->subs = nullptr; return cuda_fail(e, "output allocation"); }
+            st->owned_subs = out->subs;
+            out->subs_capacity = h->nnz_out;
+        }
+    } else {
+        if (dense_out && out->vals_capacity < cap_vals)
+            return fail(TTV_ERR_CAPACITY, "dense result needs %lld values", (long long)cap_vals);
+        if (!dense_out && p0.nr > 0 && !out->subs) return fail(TTV_ERR_ARG, "caller buffers need subs too");
+    }
+    const int64_t cap_rows = dense_out ? 0 : std::min(out->subs_capacity, out->vals_capacity);
+    const int64_t cap_rows_eff = (!dense_out && p0.nr == 0) ? out->vals_capacity : cap_rows;
+
+    const size_t need = prepared_ws_bytes(h);
+    void* ws = nullptr;
+    bool own_ws = false;
+    if (o->workspace && o->workspace_bytes >= need) {
+        ws = o->workspace;
+    } else {
+        e = cudaMallocAsync(&ws, need, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
+        own_ws = true;
+    }
+    Arena a;
+    a.base = static_cast<char*>(ws);
+    Status* status = a.take<Status>(1);
+    void* state = a.take<char>(rbk_state_bytes(h->nnz));
+    StreamDesc p = p0;
+    p.status = status;
+    cudaMemsetAsync(status, 0, sizeof(Status), stream);
+    double* ovals = static_cast<double*>(out->vals);
+    if (dense_out) cudaMemsetAsync(ovals, 0, (size_t)std::max<int64_t>(cap_vals, 1) * sizeof(double), stream);
+    if (h->nnz > 0) {
+        PrepTerms terms{};
+        terms.vals = h->vals;
+        terms.val_f32 = p0.val_f32;
+        terms.vec_f32 = vd == TTV_F32;
+        terms.n_v = h->n_v;
+        for (int j = 0; j < h->n_v; ++j) {
+            terms.sub[j] = h->subs[j];
+            terms.vec[j] = vecs[h->arg_of[j]];
+        }
+        SegOut so{out->subs, ovals, cap_rows_eff, dense_out ? 1 : 0, 0};
+        launch_reduce_by_key_prepared(h->keys, terms, h->nnz, state, p, so, status, stream);
+    }
+    if (order0) {
+        st->dense_out = 1;
+        out->nnz = 1;
+    }
+    e = cudaMemcpyAsync(st->hstatus, status, sizeof(Status), cudaMemcpyDeviceToHost, stream);
+    if (own_ws) cudaFreeAsync(ws, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "status copy");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (o->async) return TTV_OK;
+    return finalize(out);
+}
+
 static void init_once() {
     static std::once_flag f;
     std::call_once(f, [] {
@@ -843,6 +963,168 @@ void ttv_tune_clear(void) {
 int ttv_tune_count(void) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     return (int)g_tune.size();
+}
+
+// ---- prepared tensors ------------------------------------------------------
+
+int ttv_prepare(const ttv_tensor* t, const int32_t* modes, int32_t n_v, ttv_prepared** out, ttv_stream_t stream_) {
+    g_err.clear();
+    if (!out) return fail(TTV_ERR_ARG, "null result handle");
+    *out = nullptr;
+    init_once();
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    ttv_opts o;
+    ttv_opts_init(&o);
+    o.path = TTV_PATH_SORT;
+    std::vector<const void*> dummy((size_t)std::max(n_v, 0), reinterpret_cast<const void*>(0x10));
+    Plan pl;
+    int rc = make_plan(t, modes, n_v, dummy.data(), TTV_F64, nullptr, &o, pl);
+    if (rc != TTV_OK) return rc;
+    const StreamDesc& p0 = pl.desc;
+    if (p0.nnz > kMaxSortN) return fail(TTV_ERR_UNSUPPORTED, "prepared tensors support nnz < 2^30");
+    for (int m = 0; m < p0.d; ++m)
+        if (((p0.smask >> m) & 1u) && p0.shape[m] > INT32_MAX)
+            return fail(TTV_ERR_UNSUPPORTED, "contracted mode %d is larger than 2^31 - 1", m);
+    ttv_prepared* h = new ttv_prepared();
+    h->plan = pl;
+    h->plan.desc.vec_smem = 0;
+    for (int m = 0; m < TTV_MAX_D; ++m) h->plan.desc.vec[m] = nullptr;
+    h->nnz = p0.nnz;
+    h->n_v = n_v;
+    // j-th contracted mode in increasing order <- the caller's vector index
+    {
+        int j = 0;
+        for (int m = 0; m < p0.d; ++m)
+            if ((p0.smask >> m) & 1u) {
+                for (int i = 0; i < n_v; ++i)
+                    if (modes[i] == m) h->arg_of[j] = i;
+                ++j;
+            }
+    }
+    const int64_t n = std::max<int64_t>(p0.nnz, 1);
+    const size_t vb = p0.val_f32 ? 4 : 8;
+    cudaError_t e = cudaMalloc(&h->keys, (size_t)n * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&h->vals, (size_t)n * vb);
+    for (int j = 0; j < n_v && e == cudaSuccess; ++j) e = cudaMalloc(&h->subs[j], (size_t)n * 4);
+    h->bytes = (size_t)n * (8 + vb + 4 * (size_t)n_v);
+    auto drop = [&](int code, const char* what) {
+        ttv_prepared_free(h);
+        return code == TTV_ERR_CUDA ? cuda_fail(e, what) : code;
+    };
+    if (e != cudaSuccess) return drop(TTV_ERR_CUDA, "prepared tensor allocation");
+    if (p0.nnz == 0) {
+        *out = h;
+        return TTV_OK;
+    }
+    // temporaries: the second key buffer, the index payloads, the sort state
+    const int npass = (pl.key_bits + 7) / 8;
+    const int64_t ntiles = (n + 4095) / 4096;
+    Arena a;
+    a.take<Status>(1);
+    a.take<unsigned long long>(1);
+    a.take<uint64_t>(n);
+    a.take<double>(n);
+    a.take<double>(n);
+    a.take<uint32_t>((size_t)std::max(npass, 1) * 256);
+    a.take<uint32_t>((size_t)std::max(npass, 1) * ntiles * 256);
+    a.take<uint32_t>(64);
+    a.off = (a.off + 255) & ~size_t(255);
+    void* tmp = nullptr;
+    e = cudaMallocAsync(&tmp, a.off, stream);
+    if (e != cudaSuccess) return drop(TTV_ERR_CUDA, "prepare workspace");
+    a.base = static_cast<char*>(tmp);
+    a.off = 0;
+    Status* status = a.take<Status>(1);
+    unsigned long long* count = a.take<unsigned long long>(1);
+    uint64_t* keys_b = a.take<uint64_t>(n);
+    SortBuffers sb{};
+    // the sorted keys end in keys[npass % 2] (in keys[0] when nothing is
+    // sorted): make that the prepared array
+    const int last = (npass > 0 && p0.nnz > 1) ? npass % 2 : 0;
+    sb.keys[last] = h->keys;
+    sb.keys[1 - last] = keys_b;
+    sb.vals[0] = a.take<double>(n);
+    sb.vals[1] = a.take<double>(n);
+    sb.hist = a.take<uint32_t>((size_t)std::max(npass, 1) * 256);
+    sb.lookback = a.take<uint32_t>((size_t)std::max(npass, 1) * ntiles * 256);
+    sb.tickets = a.take<uint32_t>(64);
+    sb.npass = npass;
+    sb.ntiles = ntiles;
+    cudaMemsetAsync(status, 0, sizeof(Status), stream);
+    cudaMemsetAsync(count, 0, sizeof(unsigned long long), stream);
+    StreamDesc p = p0;
+    p.status = status;
+    launch_prep_keys(p, sb.keys[0], sb.vals[0], stream);
+    const int cur = radix_sort_pairs(sb, p.nnz, pl.key_bits, status, stream);
+    PrepTerms subs{};
+    subs.n_v = n_v;
+    for (int j = 0; j < n_v; ++j) subs.sub[j] = h->subs[j];
+    launch_prep_gather(p, sb.vals[cur], h->vals, subs, stream);
+    launch_prep_count(h->keys, p.nnz, count, stream);
+    Status hs;
+    unsigned long long hc = 0;
+    e = cudaMemcpyAsync(&hs, status, sizeof(Status), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, count, sizeof hc, cudaMemcpyDeviceToHost, stream);
+    cudaFreeAsync(tmp, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return drop(TTV_ERR_CUDA, "prepare");
+    if (sb.keys[cur] != h->keys) return drop(fail(TTV_ERR_CUDA, "internal: sorted keys in the wrong buffer"), "");
+    if (hs.err & kErrSubscript) return drop(fail(TTV_ERR_SUBSCRIPT, "a subscript is outside its mode"), "");
+    if (hs.err & kErrTimeout) return drop(fail(TTV_ERR_TIMEOUT, "a bounded device wait ran out"), "");
+    if (hs.err) return drop(fail(TTV_ERR_CUDA, "internal device check failed"), "");
+    h->nnz_out = (int64_t)hc;
+    *out = h;
+    return TTV_OK;
+}
+
+int ttv_prepared_run(const ttv_prepared* h, const void* const* vecs, const int64_t* vec_lens, ttv_dtype v_dtype,
+                     ttv_out* out, const ttv_opts* opts, ttv_stream_t stream) {
+    g_err.clear();
+    if (!h || !vecs || !out) return fail(TTV_ERR_ARG, "null prepared tensor, vectors or result");
+    if (v_dtype != TTV_F64 && v_dtype != TTV_F32) return fail(TTV_ERR_ARG, "bad vector dtype");
+    ttv_opts def;
+    ttv_opts_init(&def);
+    const ttv_opts* o = opts ? opts : &def;
+    if (o->fmt < TTV_OUT_SPARSE || o->fmt > TTV_OUT_AUTO) return fail(TTV_ERR_ARG, "bad output format");
+    if (o->accum != TTV_ACCUM_FP64)
+        return fail(TTV_ERR_UNSUPPORTED, "prepared tensors accumulate in binary64 (deterministic order)");
+    const StreamDesc& p0 = h->plan.desc;
+    int j = 0;
+    for (int m = 0; m < p0.d; ++m)
+        if ((p0.smask >> m) & 1u) {
+            const int i = h->arg_of[j++];
+            if (!vecs[i]) return fail(TTV_ERR_ARG, "null vector for mode %d", m);
+            if (vec_lens && vec_lens[i] != p0.shape[m])
+                return fail(TTV_ERR_VEC_LEN, "vector for mode %d has %lld entries, mode size is %lld", m,
+                            (long long)vec_lens[i], (long long)p0.shape[m]);
+        }
+    init_once();
+    return execute_prepared(h, vecs, v_dtype, out, o, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int ttv_prepared_info(const ttv_prepared* h, int64_t* nnz_out, int32_t* order, size_t* device_bytes) {
+    if (!h) return fail(TTV_ERR_ARG, "null prepared tensor");
+    if (nnz_out) *nnz_out = h->nnz_out;
+    if (order) *order = h->plan.desc.nr;
+    if (device_bytes) *device_bytes = h->bytes;
+    return TTV_OK;
+}
+
+int ttv_prepared_workspace_size(const ttv_prepared* h, size_t* bytes) {
+    if (!h || !bytes) return fail(TTV_ERR_ARG, "null argument");
+    *bytes = prepared_ws_bytes(h);
+    return TTV_OK;
+}
+
+void ttv_prepared_free(ttv_prepared* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    if (h->keys) cudaFree(h->keys);
+    if (h->vals) cudaFree(h->vals);
+    for (int j = 0; j < TTV_MAX_D; ++j)
+        if (h->subs[j]) cudaFree(h->subs[j]);
+    delete h;
 }
 
 }  // extern "C"

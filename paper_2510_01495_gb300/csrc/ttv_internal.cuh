@@ -336,6 +336,18 @@ struct SortBuffers {
 };
 
 size_t sort_workspace_bytes(int64_t n, int bits);
+
+// Terms of a prepared tensor (see ttv_prepare): values and the contracted
+// modes' subscripts stored in key order, the contracted modes in increasing
+// order with their vectors.
+struct PrepTerms {
+    const void* vals;
+    int32_t val_f32;
+    int32_t vec_f32;
+    int32_t n_v;
+    const int32_t* sub[kMaxD];
+    const void* vec[kMaxD];
+};
 // Sorts (keys, vals) stably by the low `bits` bits of the key; returns which
 // buffer (0/1) holds the result.  With n_dev, the pair count is
 // min(n, *n_dev), read on the device (n is then the upper bound the buffers

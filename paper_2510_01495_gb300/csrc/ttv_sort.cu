@@ -515,28 +515,106 @@ struct RbkPairs {
     double open;
 };
 
-__device__ __forceinline__ void rbk_load(const uint64_t* __restrict__ keys, const double* __restrict__ vals,
-                                         int64_t n, int64_t tile, RbkPairs& r) {
+// Terms of the sort path: stored next to the sorted keys.
+struct PairTerms {
+    const double* vals;
+    __device__ __forceinline__ void load(int64_t g0, int nmine, double* v) const {
+        if (nmine == kRbkItems) {
+            // the pair buffers are 16-byte aligned and g0 is a multiple of 8
+#pragma unroll
+            for (int q = 0; q < kRbkItems / 2; ++q) {
+                const double2 vv = __ldcs(reinterpret_cast<const double2*>(vals + g0) + q);
+                v[2 * q] = vv.x;
+                v[2 * q + 1] = vv.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kRbkItems; ++i) v[i] = i < nmine ? vals[g0 + i] : 0.0;
+        }
+    }
+};
+
+// Terms of a prepared tensor: formed on the fly from the value and the
+// contracted modes' subscripts stored in key order, the product taken in
+// increasing mode order exactly as the streaming kernels take it.
+struct PrepTermsDev {
+    PrepTerms t;
+    __device__ __forceinline__ double x(int j, int32_t s) const {
+        return t.vec_f32 ? (double)__ldg(static_cast<const float*>(t.vec[j]) + s)
+                         : __ldg(static_cast<const double*>(t.vec[j]) + s);
+    }
+    __device__ __forceinline__ void load(int64_t g0, int nmine, double* v) const {
+        if (t.n_v == 1 && nmine == kRbkItems) {
+            // one vector, a full run of 8: 16-byte loads of the values and
+            // subscripts (the arrays are 256-byte aligned, g0 a multiple of 8),
+            // then 8 independent gathers
+            int32_t sb[kRbkItems];
+#pragma unroll
+            for (int q = 0; q < kRbkItems / 4; ++q) {
+                const int4 w = __ldcs(reinterpret_cast<const int4*>(t.sub[0] + g0) + q);
+                sb[4 * q] = w.x;
+                sb[4 * q + 1] = w.y;
+                sb[4 * q + 2] = w.z;
+                sb[4 * q + 3] = w.w;
+            }
+            if (t.val_f32) {
+#pragma unroll
+                for (int q = 0; q < kRbkItems / 4; ++q) {
+                    const float4 w = __ldcs(reinterpret_cast<const float4*>(static_cast<const float*>(t.vals) + g0) + q);
+                    v[4 * q] = (double)w.x;
+                    v[4 * q + 1] = (double)w.y;
+                    v[4 * q + 2] = (double)w.z;
+                    v[4 * q + 3] = (double)w.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kRbkItems / 2; ++q) {
+                    const double2 w =
+                        __ldcs(reinterpret_cast<const double2*>(static_cast<const double*>(t.vals) + g0) + q);
+                    v[2 * q] = w.x;
+                    v[2 * q + 1] = w.y;
+                }
+            }
+            double xs[kRbkItems];
+#pragma unroll
+            for (int i = 0; i < kRbkItems; ++i) xs[i] = x(0, sb[i]);
+#pragma unroll
+            for (int i = 0; i < kRbkItems; ++i) v[i] = v[i] * xs[i];
+            return;
+        }
+#pragma unroll
+        for (int i = 0; i < kRbkItems; ++i) {
+            if (i < nmine) {
+                const int64_t k = g0 + i;
+                double tt = t.val_f32 ? (double)__ldcs(static_cast<const float*>(t.vals) + k)
+                                      : __ldcs(static_cast<const double*>(t.vals) + k);
+                for (int j = 0; j < t.n_v; ++j) tt = tt * x(j, __ldcs(t.sub[j] + k));
+                v[i] = tt;
+            } else {
+                v[i] = 0.0;
+            }
+        }
+    }
+};
+
+template <class Src>
+__device__ __forceinline__ void rbk_load(const uint64_t* __restrict__ keys, const Src& src, int64_t n, int64_t tile,
+                                         RbkPairs& r) {
     r.g0 = tile * kRbkTile + (int64_t)threadIdx.x * kRbkItems;
     r.nmine = (int)max((int64_t)0, min((int64_t)kRbkItems, n - r.g0));
     if (r.nmine == kRbkItems) {
-        // the pair buffers are 16-byte aligned and g0 is a multiple of 8
+        // the key buffer is 16-byte aligned and g0 is a multiple of 8
 #pragma unroll
         for (int q = 0; q < kRbkItems / 2; ++q) {
             const ulonglong2 kk = __ldcs(reinterpret_cast<const ulonglong2*>(keys + r.g0) + q);
-            const double2 vv = __ldcs(reinterpret_cast<const double2*>(vals + r.g0) + q);
             r.k[2 * q] = kk.x;
             r.k[2 * q + 1] = kk.y;
-            r.v[2 * q] = vv.x;
-            r.v[2 * q + 1] = vv.y;
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < kRbkItems; ++i) {
-            r.k[i] = i < r.nmine ? keys[r.g0 + i] : ~0ull;
-            r.v[i] = i < r.nmine ? vals[r.g0 + i] : 0.0;
-        }
+        for (int i = 0; i < kRbkItems; ++i) r.k[i] = i < r.nmine ? keys[r.g0 + i] : ~0ull;
     }
+    src.load(r.g0, r.nmine, r.v);
     r.prev0 = (r.g0 > 0 && r.nmine > 0) ? keys[r.g0 - 1] : ~0ull;   // keys are < 2^64 - 1
     r.heads = 0;
     r.cnt = 0;
@@ -609,12 +687,12 @@ __device__ __forceinline__ void rbk_block_scan(const RbkPairs& r, RbkScanSmem& s
     tv = pv;
 }
 
-__global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles(const uint64_t* __restrict__ keys,
-                                                           const double* __restrict__ vals, int64_t n,
+template <class Src>
+__global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles(const uint64_t* __restrict__ keys, Src src, int64_t n,
                                                            RbkSum* __restrict__ tiles) {
     __shared__ RbkScanSmem ss;
     RbkPairs r;
-    rbk_load(keys, vals, n, blockIdx.x, r);
+    rbk_load(keys, src, n, blockIdx.x, r);
     uint32_t xc, xf, tc, tf;
     double xv, tv;
     rbk_block_scan(r, ss, xc, xf, xv, tc, tf, tv);
@@ -729,8 +807,8 @@ struct RbkEmitSmem {
     RbkScanSmem ss;
 };
 
-__global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(const uint64_t* __restrict__ keys,
-                                                             const double* __restrict__ vals, int64_t n,
+template <class Src>
+__global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(const uint64_t* __restrict__ keys, Src src, int64_t n,
                                                              const RbkSum* __restrict__ ingroup,
                                                              const RbkSum* __restrict__ gprefix,
                                                              const unsigned long long* __restrict__ gheads,
@@ -740,7 +818,7 @@ __global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(const uint64_t* __r
     const int64_t tile = blockIdx.x;
     const int64_t ntiles = (n + kRbkTile - 1) / kRbkTile;
     RbkPairs r;
-    rbk_load(keys, vals, n, tile, r);
+    rbk_load(keys, src, n, tile, r);
     uint32_t xc, xf, tc, tf;
     double xv, tv;
     rbk_block_scan(r, sm.ss, xc, xf, xv, tc, tf, tv);
@@ -824,8 +902,9 @@ size_t rbk_state_bytes(int64_t n) {
            (size_t)ngroups * (2 * sizeof(RbkSum) + sizeof(unsigned long long)) + 512;
 }
 
-void launch_reduce_by_key(const uint64_t* keys, const double* vals, int64_t n, void* state, const StreamDesc& p,
-                          const SegOut& o, Status* st, cudaStream_t stream) {
+template <class Src>
+static void rbk_launch(const uint64_t* keys, const Src& src, int64_t n, void* state, const StreamDesc& p,
+                       const SegOut& o, Status* st, cudaStream_t stream) {
     if (n <= 0) return;
     const int64_t ntiles = (n + kRbkTile - 1) / kRbkTile;
     const int64_t ngroups = (ntiles + kRbkGroup - 1) / kRbkGroup;
@@ -837,20 +916,30 @@ void launch_reduce_by_key(const uint64_t* keys, const double* vals, int64_t n, v
     const size_t smem = sizeof(RbkEmitSmem);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_rbk_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_rbk_emit, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_rbk_emit<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_rbk_emit<Src>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
         attr_set = true;
     }
-    TTV_LAUNCH("rbk_tiles", stream, k_rbk_tiles<<<(unsigned)ntiles, kRbkThreads, 0, stream>>>(keys, vals, n, tiles));
+    TTV_LAUNCH("rbk_tiles", stream, k_rbk_tiles<Src><<<(unsigned)ntiles, kRbkThreads, 0, stream>>>(keys, src, n, tiles));
     TTV_LAUNCH("rbk_groups", stream,
                k_rbk_groups<<<(unsigned)((ngroups * 32 + 255) / 256), 256, 0, stream>>>(tiles, ntiles, ingroup, groups,
                                                                                       ngroups));
     TTV_LAUNCH("rbk_scan", stream,
                k_rbk_scan<<<1, kRbkScanThreads, 0, stream>>>(groups, ngroups, gprefix, gheads, st));
     TTV_LAUNCH("rbk_emit", stream,
-               k_rbk_emit<<<(unsigned)ntiles, kRbkThreads, smem, stream>>>(keys, vals, n, ingroup, gprefix, gheads, p,
-                                                                            o, st));
+               k_rbk_emit<Src><<<(unsigned)ntiles, kRbkThreads, smem, stream>>>(keys, src, n, ingroup, gprefix, gheads,
+                                                                                 p, o, st));
+}
+
+void launch_reduce_by_key(const uint64_t* keys, const double* vals, int64_t n, void* state, const StreamDesc& p,
+                          const SegOut& o, Status* st, cudaStream_t stream) {
+    rbk_launch(keys, PairTerms{vals}, n, state, p, o, st, stream);
+}
+
+void launch_reduce_by_key_prepared(const uint64_t* keys, const PrepTerms& terms, int64_t n, void* state,
+                                   const StreamDesc& p, const SegOut& o, Status* st, cudaStream_t stream) {
+    rbk_launch(keys, PrepTermsDev{terms}, n, state, p, o, st, stream);
 }
 
 void launch_seg_reduce(const uint64_t* keys, const double* vals, int64_t n, uint32_t* seg_start,
