@@ -22,19 +22,16 @@ void launch_dense(const StreamDesc& p, int want_presence, int compensated, int G
                   uint32_t* pres_partials, double* cell_vals, uint32_t* cell_flags, cudaStream_t stream);
 void launch_compact_cells(const StreamDesc& p, const double* cell_vals, const uint32_t* cell_flags, int64_t cap_rows,
                           int64_t* out_subs, double* out_vals, cudaStream_t stream);
-struct SegOut {
-    int64_t* subs;
-    double* vals;
-    int64_t cap_rows;
-    int dense;
-    int compensated;
-};
 void launch_seg_reduce(const uint64_t* keys, const double* vals, int64_t n, uint32_t* seg_start,
                        unsigned long long* lookback, uint32_t* ticket, uint32_t* long_list, const StreamDesc& p,
                        const SegOut& o, Status* st, cudaStream_t stream);
 size_t rbk_state_bytes(int64_t n);
-void launch_reduce_by_key_prepared(const uint64_t* keys, const PrepTerms& terms, int64_t n, void* state,
-                                   const StreamDesc& p, const SegOut& o, Status* st, cudaStream_t stream);
+void launch_reduce_by_key_prepared(const uint8_t* head_bits, const uint64_t* row_keys, const PrepTerms& terms,
+                                   int64_t n, void* state, const StreamDesc& p, const SegOut& o, Status* st,
+                                   cudaStream_t stream);
+void launch_prep_heads(const uint64_t* keys, int64_t n, uint32_t* bits, cudaStream_t stream);
+void launch_run_keys(const uint64_t* keys, const double* vals, int64_t n, void* state, uint64_t* row_keys,
+                     int64_t cap_rows, const StreamDesc& p, Status* st, cudaStream_t stream);
 void launch_prep_keys(const StreamDesc& p, uint64_t* keys, double* idx, cudaStream_t stream);
 void launch_prep_gather(const StreamDesc& p, const double* idx_sorted, void* vals_out, const PrepTerms& subs,
                         cudaStream_t stream);
@@ -565,7 +562,8 @@ struct ttv_prepared {
     int32_t arg_of[TTV_MAX_D] = {0};  // j-th contracted mode (increasing) -> caller's vector index
     int64_t nnz = 0;
     int64_t nnz_out = 0;              // distinct keys (result rows)
-    uint64_t* keys = nullptr;         // sorted keys
+    uint32_t* head_bits = nullptr;    // bit i set: nonzero i (key order) starts a result row
+    uint64_t* row_keys = nullptr;     // key of every result row
     void* vals = nullptr;             // values in key order
     int32_t* subs[TTV_MAX_D] = {nullptr};
     size_t bytes = 0;
@@ -649,12 +647,15 @@ static int execute_prepared(const ttv_prepared* h, const void* const* vecs, ttv_
         terms.val_f32 = p0.val_f32;
         terms.vec_f32 = vd == TTV_F32;
         terms.n_v = h->n_v;
-        for (int j = 0; j < h->n_v; ++j) {
-            terms.sub[j] = h->subs[j];
-            terms.vec[j] = vecs[h->arg_of[j]];
-        }
+        for (int j = 0, m = 0; m < p0.d; ++m)
+            if ((p0.smask >> m) & 1u) {
+                terms.sub[j] = h->subs[j];
+                terms.vec[j] = vecs[h->arg_of[j]];
+                ++j;
+            }
         SegOut so{out->subs, ovals, cap_rows_eff, dense_out ? 1 : 0, 0};
-        launch_reduce_by_key_prepared(h->keys, terms, h->nnz, state, p, so, status, stream);
+        launch_reduce_by_key_prepared(reinterpret_cast<const uint8_t*>(h->head_bits), h->row_keys, terms, h->nnz,
+                                      state, p, so, status, stream);
     }
     if (order0) {
         st->dense_out = 1;
@@ -1003,31 +1004,37 @@ int ttv_prepare(const ttv_tensor* t, const int32_t* modes, int32_t n_v, ttv_prep
     }
     const int64_t n = std::max<int64_t>(p0.nnz, 1);
     const size_t vb = p0.val_f32 ? 4 : 8;
-    cudaError_t e = cudaMalloc(&h->keys, (size_t)n * 8);
+    const int64_t nwords = (n + 31) / 32;
+    cudaError_t e = cudaMalloc(&h->head_bits, (size_t)nwords * 4);
     if (e == cudaSuccess) e = cudaMalloc(&h->vals, (size_t)n * vb);
     for (int j = 0; j < n_v && e == cudaSuccess; ++j) e = cudaMalloc(&h->subs[j], (size_t)n * 4);
-    h->bytes = (size_t)n * (8 + vb + 4 * (size_t)n_v);
+    h->bytes = (size_t)nwords * 4 + (size_t)n * (vb + 4 * (size_t)n_v);
     auto drop = [&](int code, const char* what) {
         ttv_prepared_free(h);
         return code == TTV_ERR_CUDA ? cuda_fail(e, what) : code;
     };
     if (e != cudaSuccess) return drop(TTV_ERR_CUDA, "prepared tensor allocation");
     if (p0.nnz == 0) {
+        e = cudaMalloc(&h->row_keys, 8);
+        if (e != cudaSuccess) return drop(TTV_ERR_CUDA, "prepared tensor allocation");
         *out = h;
         return TTV_OK;
     }
-    // temporaries: the second key buffer, the index payloads, the sort state
+    // temporaries: both key buffers, the index payloads, the sort state and
+    // the reduce-by-key state of the run-key pass
     const int npass = (pl.key_bits + 7) / 8;
     const int64_t ntiles = (n + 4095) / 4096;
     Arena a;
     a.take<Status>(1);
     a.take<unsigned long long>(1);
     a.take<uint64_t>(n);
+    a.take<uint64_t>(n);
     a.take<double>(n);
     a.take<double>(n);
     a.take<uint32_t>((size_t)std::max(npass, 1) * 256);
     a.take<uint32_t>((size_t)std::max(npass, 1) * ntiles * 256);
     a.take<uint32_t>(64);
+    a.take<char>(rbk_state_bytes(n));
     a.off = (a.off + 255) & ~size_t(255);
     void* tmp = nullptr;
     e = cudaMallocAsync(&tmp, a.off, stream);
@@ -1036,13 +1043,9 @@ int ttv_prepare(const ttv_tensor* t, const int32_t* modes, int32_t n_v, ttv_prep
     a.off = 0;
     Status* status = a.take<Status>(1);
     unsigned long long* count = a.take<unsigned long long>(1);
-    uint64_t* keys_b = a.take<uint64_t>(n);
     SortBuffers sb{};
-    // the sorted keys end in keys[npass % 2] (in keys[0] when nothing is
-    // sorted): make that the prepared array
-    const int last = (npass > 0 && p0.nnz > 1) ? npass % 2 : 0;
-    sb.keys[last] = h->keys;
-    sb.keys[1 - last] = keys_b;
+    sb.keys[0] = a.take<uint64_t>(n);
+    sb.keys[1] = a.take<uint64_t>(n);
     sb.vals[0] = a.take<double>(n);
     sb.vals[1] = a.take<double>(n);
     sb.hist = a.take<uint32_t>((size_t)std::max(npass, 1) * 256);
@@ -1050,26 +1053,40 @@ int ttv_prepare(const ttv_tensor* t, const int32_t* modes, int32_t n_v, ttv_prep
     sb.tickets = a.take<uint32_t>(64);
     sb.npass = npass;
     sb.ntiles = ntiles;
+    void* rbk_state = a.take<char>(rbk_state_bytes(n));
     cudaMemsetAsync(status, 0, sizeof(Status), stream);
     cudaMemsetAsync(count, 0, sizeof(unsigned long long), stream);
     StreamDesc p = p0;
     p.status = status;
     launch_prep_keys(p, sb.keys[0], sb.vals[0], stream);
     const int cur = radix_sort_pairs(sb, p.nnz, pl.key_bits, status, stream);
+    const uint64_t* keys = sb.keys[cur];
     PrepTerms subs{};
     subs.n_v = n_v;
     for (int j = 0; j < n_v; ++j) subs.sub[j] = h->subs[j];
     launch_prep_gather(p, sb.vals[cur], h->vals, subs, stream);
-    launch_prep_count(h->keys, p.nnz, count, stream);
+    launch_prep_heads(keys, p.nnz, h->head_bits, stream);
+    launch_prep_count(keys, p.nnz, count, stream);
     Status hs;
     unsigned long long hc = 0;
     e = cudaMemcpyAsync(&hs, status, sizeof(Status), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, count, sizeof hc, cudaMemcpyDeviceToHost, stream);
-    cudaFreeAsync(tmp, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && !(hs.err & kErrSubscript) && !hs.err) {
+        // the key of every result row
+        e = cudaMalloc(&h->row_keys, (size_t)std::max<unsigned long long>(hc, 1) * 8);
+        h->bytes += (size_t)std::max<unsigned long long>(hc, 1) * 8;
+        if (e == cudaSuccess) {
+            launch_run_keys(keys, sb.vals[cur], p.nnz, rbk_state, h->row_keys, (int64_t)hc, p, status, stream);
+            e = cudaMemcpyAsync(&hs, status, sizeof(Status), cudaMemcpyDeviceToHost, stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+            if (e == cudaSuccess) e = cudaGetLastError();
+        }
+    }
+    cudaFreeAsync(tmp, stream);
+    cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return drop(TTV_ERR_CUDA, "prepare");
-    if (sb.keys[cur] != h->keys) return drop(fail(TTV_ERR_CUDA, "internal: sorted keys in the wrong buffer"), "");
     if (hs.err & kErrSubscript) return drop(fail(TTV_ERR_SUBSCRIPT, "a subscript is outside its mode"), "");
     if (hs.err & kErrTimeout) return drop(fail(TTV_ERR_TIMEOUT, "a bounded device wait ran out"), "");
     if (hs.err) return drop(fail(TTV_ERR_CUDA, "internal device check failed"), "");
@@ -1120,7 +1137,8 @@ int ttv_prepared_workspace_size(const ttv_prepared* h, size_t* bytes) {
 void ttv_prepared_free(ttv_prepared* h) {
     if (!h) return;
     cudaDeviceSynchronize();
-    if (h->keys) cudaFree(h->keys);
+    if (h->head_bits) cudaFree(h->head_bits);
+    if (h->row_keys) cudaFree(h->row_keys);
     if (h->vals) cudaFree(h->vals);
     for (int j = 0; j < TTV_MAX_D; ++j)
         if (h->subs[j]) cudaFree(h->subs[j]);

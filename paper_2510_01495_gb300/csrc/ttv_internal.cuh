@@ -337,6 +337,18 @@ struct SortBuffers {
 
 size_t sort_workspace_bytes(int64_t n, int bits);
 
+// Where a segmented reduction writes: result rows (subs, vals) of a sparse
+// result, or vals indexed by key for a dense one; with row_keys set, only the
+// key of every run (row) is written there.
+struct SegOut {
+    int64_t* subs;          // rows of the sparse result (nullptr when dense)
+    double* vals;           // values; dense: indexed by key
+    int64_t cap_rows;       // capacity in rows (sparse)
+    int dense;
+    int compensated;
+    uint64_t* row_keys = nullptr;
+};
+
 // Terms of a prepared tensor (see ttv_prepare): values and the contracted
 // modes' subscripts stored in key order, the contracted modes in increasing
 // order with their vectors.

@@ -6,9 +6,11 @@
 // accumarray grouping), and which nonzeros fall into which row depends only
 // on the tensor, not on the vectors.  Preparing sorts the nonzeros once by
 // their key (stable: equal keys keep input order) and stores, in that order,
-// the keys, the values and the contracted modes' subscripts (int32).  A later
-// TTV with fresh vectors is then a single streaming reduce-by-key over these
-// arrays (ttv_sort.cu, PrepTerms): no radix passes.
+// the values and the contracted modes' subscripts (int32), plus a bitmap of
+// where each result row starts and each row's key.  A later TTV with fresh
+// vectors is then a single streaming reduce-by-key over these arrays
+// (ttv_sort.cu, PrepTerms with BitHeads): no radix passes, and 12 bytes read
+// per nonzero (binary64 values, one vector) instead of a key and a term.
 #include <algorithm>
 
 #include "ttv_internal.cuh"
@@ -62,6 +64,27 @@ __global__ void __launch_bounds__(256) k_prep_count(const uint64_t* __restrict__
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// head bitmap of a sorted key array: bit i of word i/32 set when i starts a run
+__global__ void __launch_bounds__(256) k_prep_heads(const uint64_t* __restrict__ keys, int64_t n,
+                                                    uint32_t* __restrict__ bits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwords = (n + 31) / 32;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords; w += warps) {
+        const int64_t i = w * 32 + lane;
+        const bool head = i < n && (i == 0 || keys[i] != keys[i - 1]);
+        const uint32_t b = __ballot_sync(0xffffffffu, head);
+        if (lane == 0) bits[w] = b;
+    }
+}
+
+void launch_prep_heads(const uint64_t* keys, int64_t n, uint32_t* bits, cudaStream_t stream) {
+    if (n <= 0) return;
+    const int64_t nwords = (n + 31) / 32;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nwords * 32 + 255) / 256, (int64_t)num_sms() * 8));
+    TTV_LAUNCH("prep_heads", stream, k_prep_heads<<<g, 256, 0, stream>>>(keys, n, bits));
 }
 
 void launch_prep_keys(const StreamDesc& p, uint64_t* keys, double* idx, cudaStream_t stream) {

@@ -372,13 +372,6 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_heads(const uint64_t* __res
         if (headbits & (1u << i)) seg_start[g++] = (uint32_t)(base + i);
 }
 
-struct SegOut {
-    int64_t* subs;          // rows of the sparse result (nullptr when dense)
-    double* vals;           // values; dense: indexed by key
-    int64_t cap_rows;       // capacity in rows (sparse)
-    int dense;
-    int compensated;
-};
 
 __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
     s = a + b;
@@ -597,11 +590,39 @@ struct PrepTermsDev {
     }
 };
 
-template <class Src>
-__device__ __forceinline__ void rbk_load(const uint64_t* __restrict__ keys, const Src& src, int64_t n, int64_t tile,
-                                         RbkPairs& r) {
+// Where the run heads come from: comparing neighbouring sorted keys, or a
+// prepared bitmap (bit i of byte i/8 set when pair i starts a run) with the
+// key of every run stored by run index.
+struct KeyHeads {
+    static constexpr bool kBits = false;
+    const uint64_t* keys;
+};
+struct BitHeads {
+    static constexpr bool kBits = true;
+    const uint8_t* bits;
+    const uint64_t* row_keys;
+};
+__device__ __forceinline__ const uint64_t* key_array(const KeyHeads& h) { return h.keys; }
+__device__ __forceinline__ const uint64_t* key_array(const BitHeads&) { return nullptr; }
+
+template <class H, class Src>
+__device__ __forceinline__ void rbk_load(const H& hd, const Src& src, int64_t n, int64_t tile, RbkPairs& r) {
     r.g0 = tile * kRbkTile + (int64_t)threadIdx.x * kRbkItems;
     r.nmine = (int)max((int64_t)0, min((int64_t)kRbkItems, n - r.g0));
+    if constexpr (H::kBits) {
+        src.load(r.g0, r.nmine, r.v);
+        // g0 is a multiple of 8: this thread's heads are one byte
+        r.heads = r.nmine > 0 ? (uint32_t)hd.bits[r.g0 >> 3] & ((1u << r.nmine) - 1u) : 0u;
+        r.prev0 = 0;
+        r.cnt = __popc(r.heads);
+        r.flag = r.heads != 0;
+        r.open = 0.0;
+#pragma unroll
+        for (int i = 0; i < kRbkItems; ++i)
+            if (i < r.nmine) r.open = ((r.heads >> i) & 1u) ? r.v[i] : r.open + r.v[i];
+        return;
+    }
+    const uint64_t* keys = key_array(hd);
     if (r.nmine == kRbkItems) {
         // the key buffer is 16-byte aligned and g0 is a multiple of 8
 #pragma unroll
@@ -687,12 +708,11 @@ __device__ __forceinline__ void rbk_block_scan(const RbkPairs& r, RbkScanSmem& s
     tv = pv;
 }
 
-template <class Src>
-__global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles(const uint64_t* __restrict__ keys, Src src, int64_t n,
-                                                           RbkSum* __restrict__ tiles) {
+template <class H, class Src>
+__global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles(H hd, Src src, int64_t n, RbkSum* __restrict__ tiles) {
     __shared__ RbkScanSmem ss;
     RbkPairs r;
-    rbk_load(keys, src, n, blockIdx.x, r);
+    rbk_load(hd, src, n, blockIdx.x, r);
     uint32_t xc, xf, tc, tf;
     double xv, tv;
     rbk_block_scan(r, ss, xc, xf, xv, tc, tf, tv);
@@ -807,8 +827,8 @@ struct RbkEmitSmem {
     RbkScanSmem ss;
 };
 
-template <class Src>
-__global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(const uint64_t* __restrict__ keys, Src src, int64_t n,
+template <class H, class Src>
+__global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(H hd, Src src, int64_t n,
                                                              const RbkSum* __restrict__ ingroup,
                                                              const RbkSum* __restrict__ gprefix,
                                                              const unsigned long long* __restrict__ gheads,
@@ -818,7 +838,7 @@ __global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(const uint64_t* __r
     const int64_t tile = blockIdx.x;
     const int64_t ntiles = (n + kRbkTile - 1) / kRbkTile;
     RbkPairs r;
-    rbk_load(keys, src, n, tile, r);
+    rbk_load(hd, src, n, tile, r);
     uint32_t xc, xf, tc, tf;
     double xv, tv;
     rbk_block_scan(r, sm.ss, xc, xf, xv, tc, tf, tv);
@@ -838,7 +858,7 @@ __global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(const uint64_t* __r
         if (i < r.nmine) {
             if ((r.heads >> i) & 1u) {
                 if (r.g0 + i > 0) {
-                    sm.row_key[h - first] = prev;
+                    if constexpr (!H::kBits) sm.row_key[h - first] = prev;
                     sm.row_val[h - first] = run;
                 }
                 ++h;
@@ -851,7 +871,7 @@ __global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(const uint64_t* __r
     }
     const bool last_tile = tile == ntiles - 1;
     if (r.nmine > 0 && r.g0 + r.nmine == n) {   // the last pair closes the last segment
-        sm.row_key[h - first] = prev;
+        if constexpr (!H::kBits) sm.row_key[h - first] = prev;
         sm.row_val[h - first] = run;
     }
     __syncthreads();
@@ -859,10 +879,14 @@ __global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(const uint64_t* __r
     const int64_t row0 = (int64_t)hb - 1 + first;
     const bool even_rows = (p.nr % 2 == 0) && ((reinterpret_cast<uintptr_t>(o.subs) & 15) == 0);
     for (int q = threadIdx.x; q < nrows; q += kRbkThreads) {
-        const uint64_t key = sm.row_key[q];
-        const double val = sm.row_val[q];
         const int64_t row = row0 + q;
-        if (o.dense) {
+        uint64_t key;
+        if constexpr (H::kBits) key = hd.row_keys[row];
+        else key = sm.row_key[q];
+        const double val = sm.row_val[q];
+        if (o.row_keys) {
+            o.row_keys[row] = key;   // only the run keys are wanted
+        } else if (o.dense) {
             o.vals[(int64_t)key] = val;
         } else if (row < o.cap_rows) {
             int64_t* dst = o.subs + row * p.nr;
@@ -894,7 +918,6 @@ __global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(const uint64_t* __r
         }
     }
 }
-
 size_t rbk_state_bytes(int64_t n) {
     const int64_t ntiles = (std::max<int64_t>(n, 1) + kRbkTile - 1) / kRbkTile;
     const int64_t ngroups = (ntiles + kRbkGroup - 1) / kRbkGroup;
@@ -902,9 +925,9 @@ size_t rbk_state_bytes(int64_t n) {
            (size_t)ngroups * (2 * sizeof(RbkSum) + sizeof(unsigned long long)) + 512;
 }
 
-template <class Src>
-static void rbk_launch(const uint64_t* keys, const Src& src, int64_t n, void* state, const StreamDesc& p,
-                       const SegOut& o, Status* st, cudaStream_t stream) {
+template <class H, class Src>
+static void rbk_launch(const H& hd, const Src& src, int64_t n, void* state, const StreamDesc& p, const SegOut& o,
+                       Status* st, cudaStream_t stream) {
     if (n <= 0) return;
     const int64_t ntiles = (n + kRbkTile - 1) / kRbkTile;
     const int64_t ngroups = (ntiles + kRbkGroup - 1) / kRbkGroup;
@@ -916,30 +939,40 @@ static void rbk_launch(const uint64_t* keys, const Src& src, int64_t n, void* st
     const size_t smem = sizeof(RbkEmitSmem);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_rbk_emit<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_rbk_emit<Src>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_rbk_emit<H, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_rbk_emit<H, Src>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
         attr_set = true;
     }
-    TTV_LAUNCH("rbk_tiles", stream, k_rbk_tiles<Src><<<(unsigned)ntiles, kRbkThreads, 0, stream>>>(keys, src, n, tiles));
+    TTV_LAUNCH("rbk_tiles", stream, k_rbk_tiles<H, Src><<<(unsigned)ntiles, kRbkThreads, 0, stream>>>(hd, src, n, tiles));
     TTV_LAUNCH("rbk_groups", stream,
                k_rbk_groups<<<(unsigned)((ngroups * 32 + 255) / 256), 256, 0, stream>>>(tiles, ntiles, ingroup, groups,
                                                                                       ngroups));
     TTV_LAUNCH("rbk_scan", stream,
                k_rbk_scan<<<1, kRbkScanThreads, 0, stream>>>(groups, ngroups, gprefix, gheads, st));
     TTV_LAUNCH("rbk_emit", stream,
-               k_rbk_emit<Src><<<(unsigned)ntiles, kRbkThreads, smem, stream>>>(keys, src, n, ingroup, gprefix, gheads,
-                                                                                 p, o, st));
+               k_rbk_emit<H, Src><<<(unsigned)ntiles, kRbkThreads, smem, stream>>>(hd, src, n, ingroup, gprefix,
+                                                                                    gheads, p, o, st));
 }
 
 void launch_reduce_by_key(const uint64_t* keys, const double* vals, int64_t n, void* state, const StreamDesc& p,
                           const SegOut& o, Status* st, cudaStream_t stream) {
-    rbk_launch(keys, PairTerms{vals}, n, state, p, o, st, stream);
+    rbk_launch(KeyHeads{keys}, PairTerms{vals}, n, state, p, o, st, stream);
 }
 
-void launch_reduce_by_key_prepared(const uint64_t* keys, const PrepTerms& terms, int64_t n, void* state,
-                                   const StreamDesc& p, const SegOut& o, Status* st, cudaStream_t stream) {
-    rbk_launch(keys, PrepTermsDev{terms}, n, state, p, o, st, stream);
+// The key of every run of a sorted key array, by run index (vals: any n
+// doubles; their sums are not written).
+void launch_run_keys(const uint64_t* keys, const double* vals, int64_t n, void* state, uint64_t* row_keys,
+                     int64_t cap_rows, const StreamDesc& p, Status* st, cudaStream_t stream) {
+    SegOut o{nullptr, nullptr, cap_rows, 0, 0};
+    o.row_keys = row_keys;
+    rbk_launch(KeyHeads{keys}, PairTerms{vals}, n, state, p, o, st, stream);
+}
+
+void launch_reduce_by_key_prepared(const uint8_t* head_bits, const uint64_t* row_keys, const PrepTerms& terms,
+                                   int64_t n, void* state, const StreamDesc& p, const SegOut& o, Status* st,
+                                   cudaStream_t stream) {
+    rbk_launch(BitHeads{head_bits, row_keys}, PrepTermsDev{terms}, n, state, p, o, st, stream);
 }
 
 void launch_seg_reduce(const uint64_t* keys, const double* vals, int64_t n, uint32_t* seg_start,
