@@ -501,6 +501,7 @@ __device__ __forceinline__ void seg_combine(uint32_t ca, uint32_t fa, double va,
 struct RbkPairs {
     uint64_t k[kRbkItems];
     double v[kRbkItems];
+    double done[kRbkItems];      // at a head: the sum of the run it closes (at the first head: of the items before it)
     uint64_t prev0;
     int nmine;
     int64_t g0;
@@ -511,6 +512,7 @@ struct RbkPairs {
 // Terms of the sort path: stored next to the sorted keys.
 struct PairTerms {
     const double* vals;
+    __device__ __forceinline__ double term(int64_t k) const { return __ldcs(vals + k); }
     __device__ __forceinline__ void load(int64_t g0, int nmine, double* v) const {
         if (nmine == kRbkItems) {
             // the pair buffers are 16-byte aligned and g0 is a multiple of 8
@@ -535,6 +537,12 @@ struct PrepTermsDev {
     __device__ __forceinline__ double x(int j, int32_t s) const {
         return t.vec_f32 ? (double)__ldg(static_cast<const float*>(t.vec[j]) + s)
                          : __ldg(static_cast<const double*>(t.vec[j]) + s);
+    }
+    __device__ __forceinline__ double term(int64_t k) const {
+        double tt = t.val_f32 ? (double)__ldcs(static_cast<const float*>(t.vals) + k)
+                              : __ldcs(static_cast<const double*>(t.vals) + k);
+        for (int j = 0; j < t.n_v; ++j) tt = tt * x(j, __ldcs(t.sub[j] + k));
+        return tt;
     }
     __device__ __forceinline__ void load(int64_t g0, int nmine, double* v) const {
         if (t.n_v == 1 && nmine == kRbkItems) {
@@ -605,6 +613,38 @@ struct BitHeads {
 __device__ __forceinline__ const uint64_t* key_array(const KeyHeads& h) { return h.keys; }
 __device__ __forceinline__ const uint64_t* key_array(const BitHeads&) { return nullptr; }
 
+// This thread's run heads in tile `tile` (bit i: pair g0 + i starts a run)
+// and its pair count, without the terms.
+template <class H>
+__device__ __forceinline__ uint32_t rbk_heads(const H& hd, int64_t n, int64_t g0, int nmine) {
+    if (nmine <= 0) return 0u;
+    if constexpr (H::kBits) {
+        return (uint32_t)hd.bits[g0 >> 3] & ((1u << nmine) - 1u);
+    } else {
+        const uint64_t* keys = key_array(hd);
+        uint64_t k[kRbkItems];
+        if (nmine == kRbkItems) {
+#pragma unroll
+            for (int q = 0; q < kRbkItems / 2; ++q) {
+                const ulonglong2 kk = __ldcs(reinterpret_cast<const ulonglong2*>(keys + g0) + q);
+                k[2 * q] = kk.x;
+                k[2 * q + 1] = kk.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kRbkItems; ++i) k[i] = i < nmine ? keys[g0 + i] : ~0ull;
+        }
+        uint64_t prev = g0 > 0 ? keys[g0 - 1] : ~0ull;
+        uint32_t heads = 0;
+#pragma unroll
+        for (int i = 0; i < kRbkItems; ++i) {
+            if (i < nmine && (k[i] != prev || g0 + i == 0)) heads |= 1u << i;
+            prev = k[i];
+        }
+        return heads;
+    }
+}
+
 template <class H, class Src>
 __device__ __forceinline__ void rbk_load(const H& hd, const Src& src, int64_t n, int64_t tile, RbkPairs& r) {
     r.g0 = tile * kRbkTile + (int64_t)threadIdx.x * kRbkItems;
@@ -616,10 +656,20 @@ __device__ __forceinline__ void rbk_load(const H& hd, const Src& src, int64_t n,
         r.prev0 = 0;
         r.cnt = __popc(r.heads);
         r.flag = r.heads != 0;
-        r.open = 0.0;
+        double acc = 0.0;
 #pragma unroll
-        for (int i = 0; i < kRbkItems; ++i)
-            if (i < r.nmine) r.open = ((r.heads >> i) & 1u) ? r.v[i] : r.open + r.v[i];
+        for (int i = 0; i < kRbkItems; ++i) {
+            r.done[i] = 0.0;
+            if (i < r.nmine) {
+                if ((r.heads >> i) & 1u) {
+                    r.done[i] = acc;
+                    acc = r.v[i];
+                } else {
+                    acc = acc + r.v[i];
+                }
+            }
+        }
+        r.open = acc;
         return;
     }
     const uint64_t* keys = key_array(hd);
@@ -640,22 +690,25 @@ __device__ __forceinline__ void rbk_load(const H& hd, const Src& src, int64_t n,
     r.heads = 0;
     r.cnt = 0;
     r.flag = 0;
-    r.open = 0.0;
+    double acc = 0.0;
     uint64_t prev = r.prev0;
 #pragma unroll
     for (int i = 0; i < kRbkItems; ++i) {
+        r.done[i] = 0.0;
         if (i < r.nmine) {
             if (r.k[i] != prev || r.g0 + i == 0) {
                 r.heads |= 1u << i;
                 ++r.cnt;
                 r.flag = 1;
-                r.open = r.v[i];
+                r.done[i] = acc;
+                acc = r.v[i];
             } else {
-                r.open = r.open + r.v[i];
+                acc = acc + r.v[i];
             }
             prev = r.k[i];
         }
     }
+    r.open = acc;
 }
 
 // Block scan of the thread summaries: each thread gets its exclusive prefix
@@ -708,19 +761,52 @@ __device__ __forceinline__ void rbk_block_scan(const RbkPairs& r, RbkScanSmem& s
     tv = pv;
 }
 
+// A tile's summary needs its head count and the sum of the terms after its
+// last head (all its terms when it has none): only the thread holding the
+// last head and the threads after it form and add terms.  The partial sums
+// are combined in a fixed order (shuffle tree, then warps left to right).
 template <class H, class Src>
 __global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles(H hd, Src src, int64_t n, RbkSum* __restrict__ tiles) {
-    __shared__ RbkScanSmem ss;
-    RbkPairs r;
-    rbk_load(hd, src, n, blockIdx.x, r);
-    uint32_t xc, xf, tc, tf;
-    double xv, tv;
-    rbk_block_scan(r, ss, xc, xf, xv, tc, tf, tv);
-    if (threadIdx.x == 0) {
+    __shared__ int s_last[kRbkThreads / 32];
+    __shared__ uint32_t s_cnt[kRbkThreads / 32];
+    __shared__ double s_val[kRbkThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t g0 = (int64_t)blockIdx.x * kRbkTile + (int64_t)tid * kRbkItems;
+    const int nmine = (int)max((int64_t)0, min((int64_t)kRbkItems, n - g0));
+    const uint32_t heads = rbk_heads(hd, n, g0, nmine);
+    // last thread with a head (-1: none) and the head count
+    const int wl = __reduce_max_sync(0xffffffffu, heads ? tid : -1);
+    const uint32_t wc = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(heads));
+    if (lane == 0) {
+        s_last[warp] = wl;
+        s_cnt[warp] = wc;
+    }
+    __syncthreads();
+    int last = -1;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kRbkThreads / 32; ++w) {
+        last = max(last, s_last[w]);
+        cnt += s_cnt[w];
+    }
+    double c = 0.0;
+    if (tid >= last && nmine > 0) {
+        const int start = tid == last ? 31 - __clz(heads) : 0;   // this thread's last head
+        c = src.term(g0 + start);
+        for (int i = start + 1; i < nmine; ++i) c = c + src.term(g0 + i);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) c = c + __shfl_down_sync(0xffffffffu, c, off);
+    __syncthreads();
+    if (lane == 0) s_val[warp] = c;
+    __syncthreads();
+    if (tid == 0) {
+        double v = 0.0;
+        for (int w = max(last, 0) >> 5; w < kRbkThreads / 32; ++w) v = v + s_val[w];
         RbkSum t;
-        t.val = tv;
-        t.cnt = tc;
-        t.flag = tf;
+        t.val = v;
+        t.cnt = cnt;
+        t.flag = last >= 0;
         tiles[blockIdx.x] = t;
     }
 }
@@ -847,24 +933,26 @@ __global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(H hd, Src src, int6
     const int64_t g = tile / kRbkGroup;
     const double carry = ig.flag ? ig.val : gprefix[g].val + ig.val;
     const unsigned long long hb = gheads[g] + ig.cnt;
-    double run = xf ? xv : carry + xv;
+    // value of the run open when this thread's range starts
+    const double base = xf ? xv : carry + xv;
     // a head at tile-local head index h closes the segment at row h - first
-    // of this tile (first = 1 in tile 0, whose first head closes nothing)
+    // of this tile (first = 1 in tile 0, whose first head closes nothing);
+    // the sum of a run that starts inside this thread's range was formed by
+    // rbk_load, the run open at the start adds `base` to its part here
     const int first = tile == 0 ? 1 : 0;
     int h = (int)xc;
     uint64_t prev = r.prev0;
+    bool seen = false;
 #pragma unroll
     for (int i = 0; i < kRbkItems; ++i) {
         if (i < r.nmine) {
             if ((r.heads >> i) & 1u) {
                 if (r.g0 + i > 0) {
                     if constexpr (!H::kBits) sm.row_key[h - first] = prev;
-                    sm.row_val[h - first] = run;
+                    sm.row_val[h - first] = seen ? r.done[i] : base + r.done[i];
                 }
                 ++h;
-                run = r.v[i];
-            } else {
-                run = run + r.v[i];
+                seen = true;
             }
             prev = r.k[i];
         }
@@ -872,7 +960,7 @@ __global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(H hd, Src src, int6
     const bool last_tile = tile == ntiles - 1;
     if (r.nmine > 0 && r.g0 + r.nmine == n) {   // the last pair closes the last segment
         if constexpr (!H::kBits) sm.row_key[h - first] = prev;
-        sm.row_val[h - first] = run;
+        sm.row_val[h - first] = r.flag ? r.open : base + r.open;
     }
     __syncthreads();
     const int nrows = (int)tc - first + (last_tile ? 1 : 0);
