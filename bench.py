@@ -640,20 +640,41 @@ def run_serve(args, rank, world, local_rank):
     srv.reset_stats()
     clocks = _clock_start(local_rank)
     arrivals = np.cumsum(g.exponential(1.0 / args.rate, size=args.requests))
-    rids = []
-    barrier(dist)
-    t0 = time.perf_counter()
-    for k, (ti, m, x) in enumerate(reqs[64:]):
-        delay = arrivals[k] - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        rids.append(srv.submit(ids[ti], [m], [x], accum="compensated"))
-    for r in rids:
-        srv.wait(r)
-    wall = time.perf_counter() - t0
-    barrier(dist)
-    wall = max_over_ranks(dist, wall, dev)
+
+    def stream(accum):
+        rids = []
+        barrier(dist)
+        t0 = time.perf_counter()
+        for k, (ti, m, x) in enumerate(reqs[64:]):
+            delay = arrivals[k] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            rids.append(srv.submit(ids[ti], [m], [x], accum=accum))
+        for r in rids:
+            srv.wait(r)
+        w = time.perf_counter() - t0
+        barrier(dist)
+        return max_over_ranks(dist, w, dev)
+
+    wall = stream("compensated")
     st = srv.stats()
+    # the same stream on prepared layouts (every mode of every tensor, as far
+    # as the budget allows; prepared runs accumulate in binary64)
+    t_prep = time.perf_counter()
+    n_prep = 0
+    for tid in ids:
+        for m in range(4):
+            try:
+                srv.prepare(tid, [m])
+                n_prep += 1
+            except ttv.TTVError:
+                pass
+    t_prep = time.perf_counter() - t_prep
+    for ti, m, x in reqs[:64]:
+        srv.wait(srv.submit(ids[ti], [m], [x], accum="fp64"))
+    srv.reset_stats()
+    wall_p = stream("fp64")
+    st_p = srv.stats()
     clk = clocks.stop()
     served_nnz = sum_over_ranks(dist, sum(nnzs[ti] for ti, _, _ in reqs[64:]), dev)
     n_plain = min(300, args.requests)
@@ -697,6 +718,12 @@ def run_serve(args, rank, world, local_rank):
                    "budget_bytes": 60 << 30},
         "serve": {"p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
                   "throughput_rps": args.requests * world / wall, "completed": st["completed"]},
+        "serve_prepared": {"p50_ms": st_p["p50_us"] / 1e3, "p99_ms": st_p["p99_us"] / 1e3,
+                           "throughput_rps": args.requests * world / wall_p,
+                           "throughput_gnnz_s": sum_over_ranks(dist, sum(nnzs[ti] for ti, _, _ in reqs[64:]), dev)
+                           / wall_p / 1e9,
+                           "prepared_runs": st_p["prepared_runs"], "layouts": n_prep, "prepare_s": round(t_prep, 2),
+                           "accum": "fp64 (prepared runs)"},
         "plain": {"requests": n_plain, "throughput_rps": n_plain / wall_plain,
                   "throughput_gnnz_s": plain_nnz / wall_plain / 1e9, "p50_ms": pst["p50_us"] / 1e3,
                   "p99_ms": pst["p99_us"] / 1e3},

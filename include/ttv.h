@@ -306,6 +306,7 @@ typedef struct {
     double seconds;                           /* since creation or reset          */
     double throughput_rps, throughput_gnnz_s; /* completed requests / nonzeros    */
     size_t bytes_in_use, budget_bytes;
+    long long prepared_runs;                  /* requests served from a prepared layout */
 } ttv_stats;
 
 /* budget_bytes bounds resident tensors + in-flight requests; n_slots (1..64)
@@ -315,6 +316,14 @@ int ttv_server_create(size_t budget_bytes, int32_t n_slots, ttv_server **server)
  * against the budget until the server is destroyed.  TTV_ERR_BUDGET if it
  * does not fit. */
 int ttv_server_register(ttv_server *server, const ttv_tensor *t, int32_t *tensor_id);
+/* Prepares registered tensor `tensor_id` for TTVs along exactly the modes
+ * given (see ttv_prepare; the layout counts against the budget until the
+ * server is destroyed).  Later requests on that tensor with the same set of
+ * modes (any order), fp64 accumulation and path AUTO run on the prepared
+ * layout: results identical to the sort path, no sort passes.  Synchronous;
+ * TTV_ERR_BUDGET if the layout does not fit, errors of ttv_prepare
+ * otherwise.  May be called while requests run. */
+int ttv_server_prepare(ttv_server *server, int32_t tensor_id, const int32_t *modes, int32_t n_v);
 /* Queues a TTV of registered tensor `tensor_id` with n_v host vectors (each
  * shape[modes[i]] entries of v_dtype, copied at submit).  opts may be NULL
  * (its workspace and async fields are ignored).  TTV_ERR_BUDGET if the request

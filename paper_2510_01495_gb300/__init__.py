@@ -643,7 +643,8 @@ class Stats(ctypes.Structure):
                 ("max_us", ctypes.c_double), ("completed", ctypes.c_longlong), ("admitted", ctypes.c_longlong),
                 ("refused", ctypes.c_longlong), ("pending", ctypes.c_longlong), ("seconds", ctypes.c_double),
                 ("throughput_rps", ctypes.c_double), ("throughput_gnnz_s", ctypes.c_double),
-                ("bytes_in_use", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t)]
+                ("bytes_in_use", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+                ("prepared_runs", ctypes.c_longlong)]
 
 
 def _declare_serve(lib):
@@ -654,6 +655,8 @@ def _declare_serve(lib):
     lib.ttv_server_create.restype = ctypes.c_int
     lib.ttv_server_register.argtypes = [ctypes.c_void_p, P(Tensor), P(ctypes.c_int32)]
     lib.ttv_server_register.restype = ctypes.c_int
+    lib.ttv_server_prepare.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int32), ctypes.c_int32]
+    lib.ttv_server_prepare.restype = ctypes.c_int
     lib.ttv_server_submit.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int32), ctypes.c_int32,
                                       P(ctypes.c_void_p), ctypes.c_int, P(Opts), P(ctypes.c_uint64)]
     lib.ttv_server_submit.restype = ctypes.c_int
@@ -718,6 +721,11 @@ class Server:
         self.shapes[int(tid.value)] = tuple(shape)
         torch.cuda.synchronize()
         return int(tid.value)
+
+    def prepare(self, tensor_id: int, modes):
+        """Prepared layout of a registered tensor for TTVs along ``modes``."""
+        m = (ctypes.c_int32 * len(modes))(*[int(x) for x in modes])
+        _check(self.lib, self.lib.ttv_server_prepare(self.h, int(tensor_id), m, len(modes)))
 
     def submit(self, tensor_id: int, modes, host_vecs, fmt="sparse", accum="fp64", path="auto") -> int:
         import numpy as np

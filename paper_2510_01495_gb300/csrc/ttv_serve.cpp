@@ -35,6 +35,13 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+struct PreparedModes {
+    uint32_t mask = 0;               // contracted modes
+    std::vector<int32_t> modes;      // in the order given to ttv_prepare
+    ttv_prepared* h = nullptr;
+    size_t bytes = 0;
+};
+
 struct Resident {
     int64_t* subs = nullptr;     // d columns of nnz
     void* vals = nullptr;
@@ -43,6 +50,7 @@ struct Resident {
     int32_t d = 0;
     int64_t shape[TTV_MAX_D] = {0};
     size_t bytes = 0;
+    std::vector<std::shared_ptr<PreparedModes>> prepared;
 };
 
 struct Request {
@@ -88,7 +96,7 @@ struct ttv_server {
     std::vector<Resident> tensors;
     std::vector<double> lat_us;
     uint64_t next_id = 1;
-    long long admitted = 0, refused = 0, completed = 0;
+    long long admitted = 0, refused = 0, completed = 0, prepared_runs = 0;
     double nnz_done = 0;
     Clock::time_point t0;
     bool stop = false;
@@ -102,6 +110,8 @@ void free_resident(Resident& r) {
     if (r.vals) cudaFree(r.vals);
     r.subs = nullptr;
     r.vals = nullptr;
+    for (auto& pm : r.prepared) ttv_prepared_free(pm->h);
+    r.prepared.clear();
 }
 
 // Finishes a request whose slot event has completed.
@@ -128,7 +138,18 @@ void complete(ttv_server* s, Slot& sl) {
 void start(ttv_server* s, Slot& sl, const std::shared_ptr<Request>& r) {
     sl.req = r;
     r->slot = (int)(&sl - s->slots.data());
-    const Resident& t = s->tensors[(size_t)r->tensor];
+    Resident t;
+    std::shared_ptr<PreparedModes> prep;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        t = s->tensors[(size_t)r->tensor];
+    }
+    if (r->opts.accum == TTV_ACCUM_FP64 && r->opts.path == TTV_PATH_AUTO) {
+        uint32_t mask = 0;
+        for (int32_t m : r->modes) mask |= 1u << m;
+        for (auto& pm : t.prepared)
+            if (pm->mask == mask) prep = pm;
+    }
     const size_t vbytes = r->vecs.size();
     if (sl.pinned_bytes < vbytes) {
         if (sl.pinned) cudaFreeHost(sl.pinned);
@@ -173,8 +194,24 @@ void start(ttv_server* s, Slot& sl, const std::shared_ptr<Request>& r) {
         o.async = 1;
         o.workspace = nullptr;
         o.workspace_bytes = 0;
-        r->rc = ttv_multi_checked(&tt, r->modes.data(), (int32_t)r->modes.size(), vp.data(), lens.data(), r->v_dtype,
-                                  &r->out, &o, reinterpret_cast<ttv_stream_t>(sl.stream));
+        if (prep) {
+            // vectors in the order the layout was prepared with
+            std::vector<const void*> pv(prep->modes.size());
+            std::vector<int64_t> pl(prep->modes.size());
+            for (size_t k = 0; k < prep->modes.size(); ++k)
+                for (size_t i = 0; i < r->modes.size(); ++i)
+                    if (r->modes[i] == prep->modes[k]) {
+                        pv[k] = vp[i];
+                        pl[k] = lens[i];
+                    }
+            r->rc = ttv_prepared_run(prep->h, pv.data(), pl.data(), r->v_dtype, &r->out, &o,
+                                     reinterpret_cast<ttv_stream_t>(sl.stream));
+            std::lock_guard<std::mutex> g(s->mu);
+            s->prepared_runs += 1;
+        } else {
+            r->rc = ttv_multi_checked(&tt, r->modes.data(), (int32_t)r->modes.size(), vp.data(), lens.data(),
+                                      r->v_dtype, &r->out, &o, reinterpret_cast<ttv_stream_t>(sl.stream));
+        }
     }
     cudaEventRecord(sl.done, sl.stream);
 }
@@ -299,6 +336,46 @@ int ttv_server_register(ttv_server* s, const ttv_tensor* t, int32_t* tensor_id) 
     return TTV_OK;
 }
 
+int ttv_server_prepare(ttv_server* s, int32_t tensor_id, const int32_t* modes, int32_t n_v) {
+    if (!s || !modes || n_v < 1 || n_v > TTV_MAX_D) return ttv::fail(TTV_ERR_ARG, "bad prepare request");
+    Resident t;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (tensor_id < 0 || (size_t)tensor_id >= s->tensors.size()) return ttv::fail(TTV_ERR_ARG, "unknown tensor");
+        t = s->tensors[(size_t)tensor_id];
+    }
+    ttv_tensor tt;
+    tt.subs = t.subs;
+    tt.stride_nz = 1;
+    tt.stride_mode = t.nnz;
+    tt.vals = t.vals;
+    tt.val_dtype = t.val_dtype;
+    tt.nnz = t.nnz;
+    tt.shape = t.shape;
+    tt.d = t.d;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+        return ttv::fail(TTV_ERR_CUDA, "prepare stream");
+    ttv_prepared* h = nullptr;
+    int rc = ttv_prepare(&tt, modes, n_v, &h, reinterpret_cast<ttv_stream_t>(st));
+    cudaStreamDestroy(st);
+    if (rc != TTV_OK) return rc;
+    auto pm = std::make_shared<PreparedModes>();
+    pm->h = h;
+    pm->modes.assign(modes, modes + n_v);
+    for (int32_t i = 0; i < n_v; ++i) pm->mask |= 1u << modes[i];
+    ttv_prepared_info(h, nullptr, nullptr, &pm->bytes);
+    std::lock_guard<std::mutex> g(s->mu);
+    if (s->in_use + pm->bytes > s->budget) {
+        ttv_prepared_free(h);
+        return ttv::fail(TTV_ERR_BUDGET, "prepared layout (%zu bytes) does not fit the budget", pm->bytes);
+    }
+    s->in_use += pm->bytes;
+    s->tensors[(size_t)tensor_id].bytes += pm->bytes;
+    s->tensors[(size_t)tensor_id].prepared.push_back(pm);
+    return TTV_OK;
+}
+
 int ttv_server_submit(ttv_server* s, int32_t tensor_id, const int32_t* modes, int32_t n_v,
                       const void* const* host_vecs, ttv_dtype v_dtype, const ttv_opts* opts, uint64_t* req_id) {
     if (!s || !modes || !host_vecs || !req_id || n_v < 1) return ttv::fail(TTV_ERR_ARG, "bad request");
@@ -394,6 +471,7 @@ int ttv_server_stats(ttv_server* s, ttv_stats* st) {
     st->throughput_gnnz_s = secs > 0 ? s->nnz_done / secs / 1e9 : 0;
     st->bytes_in_use = s->in_use;
     st->budget_bytes = s->budget;
+    st->prepared_runs = s->prepared_runs;
     return TTV_OK;
 }
 
@@ -404,6 +482,7 @@ int ttv_server_reset_stats(ttv_server* s) {
     s->completed = 0;
     s->admitted = 0;
     s->refused = 0;
+    s->prepared_runs = 0;
     s->nnz_done = 0;
     s->t0 = Clock::now();
     return TTV_OK;

@@ -135,3 +135,31 @@ def test_server_budget_and_timeout(cuda_lib):
         srv.wait(123456, timeout_us=1000)
     assert e.value.name == "TTV_ERR_TIMEOUT"
     srv.close()
+
+
+def test_server_prepared_layouts(cuda_lib):
+    # requests on a prepared (tensor, modes) run on the prepared layout: the
+    # result equals the sort path bit for bit; other requests are unaffected
+    dev = "cuda"
+    t = S.sptenrand(81, (200, 300, 400, 50), 150_000, vals="u11")
+    subs, vals = t.subs.to(dev), t.vals.to(dev)
+    srv = cuda_lib.Server(budget_bytes=4 << 30, slots=4)
+    tid = srv.register(subs, vals, t.shape)
+    srv.prepare(tid, [1])
+    srv.prepare(tid, [3, 0])
+    g = np.random.default_rng(9)
+    cases = [([1], [g.uniform(-1, 1, 300)]),
+             ([0, 3], [g.uniform(-1, 1, 200), g.uniform(-1, 1, 50)]),
+             ([2], [g.uniform(-1, 1, 400)])]
+    rids = [srv.submit(tid, modes, xs) for modes, xs in cases]
+    results = [srv.wait(r) for r in rids]
+    st = srv.stats()
+    assert st["prepared_runs"] == 2
+    for (modes, xs), res in zip(cases, results):
+        xd = [torch.from_numpy(x).to(dev) for x in xs]
+        ref, A = oracle_ttv(subs, vals, t.shape, modes, xd)
+        check_result(res, ref, A, what=f"server prepared {modes}")
+        s = cuda_lib.ttv_multi(subs, vals, t.shape, modes, xd, path="sort")
+        if modes != [2]:
+            assert torch.equal(res.vals, s.vals) and torch.equal(res.subs, s.subs)
+    srv.close()
