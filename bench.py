@@ -88,8 +88,8 @@ TRAFFIC = {
     "allbutone_4way_1000": {
         "kernel": "dense_accum",
         "files": ["ttv_dense_vec.cu", "ttv_internal.cuh", "ttv_udiv.h"],
-        "sha": "e543b9c2e857",
-        "bytes_per_launch": 400338984,   # 400.09 MB read + 0.25 MB written, mean of 45 launches
+        "sha": "d68ab89cdbab",
+        "bytes_per_launch": 400288085,   # 400.08 MB read + 0.21 MB written, mean of 45 launches
     },
 }
 
