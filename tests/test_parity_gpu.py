@@ -371,3 +371,30 @@ def test_sort_segments_spanning_many_tiles(cuda_lib, fmt):
 def test_sort_tile_edges(cuda_lib, nnz):
     p = rand_problem(500 + nnz, (300, 200, 100), nnz, [1])
     run_case(cuda_lib, p, path="sort")
+
+
+# ---- extremes: the largest order, keys above 2^63 ---------------------------------------
+
+@pytest.mark.parametrize("path", ["auto", "sort", "hash", "bucket"])
+def test_order_8(cuda_lib, path):
+    p = rand_problem(808, (5, 4, 6, 3, 7, 4, 5, 6), 30_000, [2, 5])
+    run_case(cuda_lib, p, path=path, layout="soa")
+    q = rand_problem(809, (5, 4, 6, 3, 7, 4, 5, 6), 20_000, [0, 1, 2, 3, 4, 6, 7])
+    run_case(cuda_lib, q, path=path, fmt="dense" if path == "auto" else "sparse")
+
+
+@pytest.mark.parametrize("path", ["sort", "hash", "bucket"])
+def test_keys_above_2_63(cuda_lib, path):
+    # surviving key space 65535 * 65536^3 ~ 1.8e19: keys use the top bit of
+    # uint64 and must be ordered as unsigned everywhere
+    g = np.random.default_rng(12)
+    n = 40_000
+    shape = (65535, 65536, 65536, 65536, 7)
+    subs = np.stack([g.integers(0, s, n) for s in shape], axis=1)
+    subs[: n // 2, 0] = g.integers(32768, 65535, n // 2)       # half the keys >= 2^63
+    subs[100:140] = subs[100]                                   # a repeated tuple
+    vals = g.uniform(-1, 1, n)
+    x = g.uniform(-1, 1, 7)
+    p = S.Problem(S.SparseTensor(torch.from_numpy(subs), torch.from_numpy(vals), shape), [4],
+                  [torch.from_numpy(x)], name="top_bit_keys")
+    run_case(cuda_lib, p, path=path, layout="soa")
