@@ -1,12 +1,13 @@
-"""CPU oracle for the sparse tensor-times-vector product (paper Sec. 3.3, Eq. 3).
+"""CPU oracle for the sparse tensor-times-vector product (paper Sec. 3.3, Eq. 3)
+and for the MTTKRP built on it (named in Sec. 3.3 and Sec. 5).
 
 TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it; the CUDA
 library (``paper_2510_01495_gb300``) neither imports nor links it, and this
 package imports nothing from the library.
 
-``ttv`` wraps the plain C statement in ``ttv_oracle.c`` (built with gcc and
-``-ffp-contract=off``).  It upcasts float32 inputs to float64 exactly before
+``ttv`` and ``mttkrp`` wrap the plain C statements in ``ttv_oracle.c``
+(built with gcc and ``-ffp-contract=off``).  It upcasts float32 inputs to float64 exactly before
 the call, so an FP32-stored tensor is evaluated as the exact FP64 values it
 holds.  Parity status of every function here: pinned (see tests/test_oracle_pins.py).
 """
@@ -83,6 +84,12 @@ def load_library(path: str):
         ctypes.POINTER(_Out)]
     lib.oracle_free.restype = None
     lib.oracle_free.argtypes = [ctypes.POINTER(_Out)]
+    lib.oracle_mttkrp.restype = ctypes.c_int
+    lib.oracle_mttkrp.argtypes = [
+        ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+        ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
+        ctypes.POINTER(ctypes.c_double)]
     return lib
 
 
@@ -155,3 +162,44 @@ def ttv(subs, vals, shape, modes, vecs, dense: bool = False, lib=None):
         return subs_out, vals_out, newshape
     finally:
         lib.oracle_free(ctypes.byref(out))
+
+
+def mttkrp(subs, vals, shape, mode: int, factors, lib=None) -> np.ndarray:
+    """MTTKRP along ``mode`` by the plain definition: ``factors`` holds one
+    (shape[m], rank) matrix per mode (the entry for ``mode`` is ignored and may
+    be None); returns the (shape[mode], rank) float64 result."""
+    lib = lib or _get_lib()
+    shape = np.ascontiguousarray(np.asarray(shape, dtype=np.int64).reshape(-1))
+    d = int(shape.size)
+    subs = np.ascontiguousarray(np.asarray(subs, dtype=np.int64).reshape(-1, d))
+    vals = _as_f64(vals).reshape(-1)
+    if subs.shape[0] != vals.shape[0]:
+        raise ValueError("subs and vals disagree on nnz")
+    mode = int(mode)
+    rank = None
+    mats = []
+    for m in range(d):
+        if m == mode:
+            mats.append(None)
+            continue
+        a = _as_f64(factors[m])
+        if a.ndim != 2 or a.shape[0] != shape[m]:
+            raise ValueError(f"factor {m} must be ({shape[m]}, rank)")
+        if rank is None:
+            rank = a.shape[1]
+        if a.shape[1] != rank:
+            raise ValueError("factors disagree on the rank")
+        mats.append(np.ascontiguousarray(a))
+    if rank is None:
+        raise ValueError("no factor matrices")
+    nullp = ctypes.POINTER(ctypes.c_double)()
+    ptr_arr = (ctypes.POINTER(ctypes.c_double) * d)(
+        *[nullp if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in mats])
+    out = np.zeros((int(shape[mode]), rank), dtype=np.float64)
+    rc = lib.oracle_mttkrp(d, shape.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(vals.size),
+                           subs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                           vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), mode, rank, ptr_arr,
+                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise OracleError(rc)
+    return out

@@ -226,3 +226,62 @@ int oracle_ttv(int32_t d, const int64_t *shape, int64_t nnz,
     out->vals = dv;
     return ORACLE_OK;
 }
+
+/*
+ * Matricized tensor times Khatri-Rao product (MTTKRP) along mode `mode`.
+ * The paper names it as the kernel built on the sparse TTV (Sec. 3.3) and as
+ * future work (Sec. 5) without writing it out; this is the standard
+ * definition.  With factor matrices A_m (shape[m] x rank, row-major) for
+ * every m != mode:
+ *
+ *     M(i, r) = sum over k with subs[k, mode] == i of
+ *               vals[k] * prod_{m != mode, increasing} A_m(subs[k, m], r)
+ *
+ * so column r of M is the all-but-one TTV (Eq. 3 with n_v = d - 1) of the
+ * tensor with the vectors A_m(:, r), m != mode.  Each (i, r) is summed in
+ * input order with Neumaier's compensated summation, like the TTV groups
+ * above, and rows i that no nonzero touches are 0.
+ *
+ * factors   d pointers; factors[mode] is not read
+ * out       shape[mode] x rank doubles, row-major (written in full)
+ * Returns ORACLE_OK or a negative ORACLE_ERR_*.
+ */
+int oracle_mttkrp(int32_t d, const int64_t *shape, int64_t nnz, const int64_t *subs, const double *vals,
+                  int32_t mode, int32_t rank, const double *const *factors, double *out)
+{
+    if (!shape || d < 1 || d > ORACLE_MAX_D || nnz < 0 || rank < 1 || !factors || !out) return ORACLE_ERR_ARG;
+    if (mode < 0 || mode >= d) return ORACLE_ERR_MODE;
+    if (nnz > 0 && (!subs || !vals)) return ORACLE_ERR_ARG;
+    for (int32_t m = 0; m < d; ++m) {
+        if (shape[m] < 1) return ORACLE_ERR_ARG;
+        if (m != mode && !factors[m]) return ORACLE_ERR_ARG;
+    }
+    for (int64_t k = 0; k < nnz; ++k)
+        for (int32_t m = 0; m < d; ++m)
+            if (subs[k * d + m] < 0 || subs[k * d + m] >= shape[m]) return ORACLE_ERR_SUBSCRIPT;
+
+    const int64_t rows = shape[mode];
+    double *comp = (double *)calloc((size_t)rows * (size_t)rank, sizeof(double));
+    if (!comp) return ORACLE_ERR_NOMEM;
+    for (int64_t q = 0; q < rows * rank; ++q) out[q] = 0.0;
+
+    /* input order: every (i, r) sum receives its terms in increasing k */
+    for (int64_t k = 0; k < nnz; ++k) {
+        const int64_t i = subs[k * d + mode];
+        for (int32_t r = 0; r < rank; ++r) {
+            double t = vals[k];
+            for (int32_t m = 0; m < d; ++m)
+                if (m != mode) t = t * factors[m][subs[k * d + m] * rank + r];
+            double *sum = &out[i * rank + r];
+            double *c = &comp[i * rank + r];
+            const double s = *sum + t;
+            if (fabs(*sum) >= fabs(t)) *c += (*sum - s) + t;
+            else                       *c += (t - s) + *sum;
+            *sum = s;
+        }
+    }
+    for (int64_t q = 0; q < rows * rank; ++q)
+        if (isfinite(out[q])) out[q] += comp[q];
+    free(comp);
+    return ORACLE_OK;
+}

@@ -301,3 +301,72 @@ ALL_CHECKS = [
     check_ones_vector_is_mode_sum, check_linearity, check_all_modes_multilinear,
     check_mode_order_independence, check_support_and_order, check_dense_matches_sparse,
 ]
+
+
+# ---- MTTKRP (named in Sec. 3.3 and Sec. 5; the standard definition) ----------------
+
+def mttkrp_case(seed, d, rank, dyadic=False):
+    subs, vals, shape, _ = random_case(seed, d, dyadic=dyadic)
+    g = rng(5000 + seed)
+    if dyadic:
+        facs = [g.integers(-8, 9, size=(n, rank)).astype(np.float64) / 8.0 for n in shape]
+    else:
+        facs = [g.uniform(-1, 1, size=(n, rank)) for n in shape]
+    mode = int(g.integers(0, d))
+    return subs, vals, shape, facs, mode
+
+
+def mttkrp_brute_force(subs, vals, shape, mode, facs):
+    """M(i, r) exactly, term by term over the nonzeros (duplicates included)."""
+    rank = facs[(mode + 1) % len(shape)].shape[1]
+    out = [[Fraction(0)] * rank for _ in range(shape[mode])]
+    for k in range(len(vals)):
+        for r in range(rank):
+            t = Fraction(float(vals[k]))
+            for m in range(len(shape)):
+                if m != mode:
+                    t *= Fraction(float(facs[m][int(subs[k, m]), r]))
+            out[int(subs[k, mode])][r] += t
+    return out
+
+
+def check_mttkrp_equals_ttv_columns(mttkrp, ttv):
+    """Column r of the MTTKRP is the all-but-one TTV with the factor columns
+    A_m(:, r) as vectors: same products, same groups, same summation order,
+    so equal bit for bit."""
+    for seed in range(30):
+        d = 2 + seed % 4
+        subs, vals, shape, facs, mode = mttkrp_case(seed, d, rank=1 + seed % 5)
+        M = mttkrp(subs, vals, shape, mode, facs)
+        modes = [m for m in range(d) if m != mode]
+        for r in range(M.shape[1]):
+            _, col, _ = ttv(subs, vals, shape, modes, [facs[m][:, r] for m in modes], dense=True)
+            assert np.array_equal(M[:, r], col), (seed, r)
+
+
+def check_mttkrp_bruteforce_exact(mttkrp, ttv=None):
+    for seed in range(30):
+        d = 1 + seed % 4
+        if d == 1:
+            d = 2
+        subs, vals, shape, facs, mode = mttkrp_case(seed + 300, d, rank=3, dyadic=True)
+        M = mttkrp(subs, vals, shape, mode, facs)
+        ref = mttkrp_brute_force(subs, vals, shape, mode, facs)
+        assert M.shape == (shape[mode], 3)
+        assert [[Fraction(float(x)) for x in row] for row in M] == ref, seed
+
+
+def check_mttkrp_bruteforce_rounded(mttkrp, ttv=None):
+    for seed in range(30):
+        d = 2 + seed % 3
+        subs, vals, shape, facs, mode = mttkrp_case(seed + 600, d, rank=4)
+        M = mttkrp(subs, vals, shape, mode, facs)
+        ref = mttkrp_brute_force(subs, vals, shape, mode, facs)
+        absref = mttkrp_brute_force(subs, np.abs(vals), shape, mode, [np.abs(f) for f in facs])
+        for i in range(shape[mode]):
+            for r in range(4):
+                bound = (d + 1) * EPS * float(absref[i][r]) + 2 * EPS * abs(float(ref[i][r]))
+                assert abs(Fraction(float(M[i, r])) - ref[i][r]) <= Fraction(bound) * (1 + 1e-12), (seed, i, r)
+
+
+MTTKRP_CHECKS = [check_mttkrp_equals_ttv_columns, check_mttkrp_bruteforce_exact, check_mttkrp_bruteforce_rounded]

@@ -36,6 +36,33 @@ MUTANTS = {
                            "lin = lin + gsubs[q * ctx.nr + j] * (j == 0 ? 1 : out->shape[j - 1]);"),
 }
 
+MTTKRP_MUTANTS = {
+    "mttkrp_skips_a_mode": ("if (m != mode) t = t * factors[m][subs[k * d + m] * rank + r];",
+                            "if (m != mode && m != d - 1) t = t * factors[m][subs[k * d + m] * rank + r];"),
+    "mttkrp_wrong_factor_row": ("if (m != mode) t = t * factors[m][subs[k * d + m] * rank + r];",
+                                "if (m != mode) t = t * factors[m][(subs[k * d + m] % shape[m]) * rank + 0];"),
+    "mttkrp_wrong_output_row": ("const int64_t i = subs[k * d + mode];",
+                                "const int64_t i = subs[k * d + mode] == 0 ? 0 : subs[k * d + mode] - 1;"),
+    "mttkrp_no_compensation": ("if (fabs(*sum) >= fabs(t)) *c += (*sum - s) + t;\n            else                       *c += (t - s) + *sum;",
+                               ""),
+}
+
+RUNNER_MTTKRP = r"""
+import sys
+sys.path.insert(0, {root!r}); sys.path.insert(0, {tests!r})
+import oracle, oracle_pins as P
+lib = oracle.load_library({lib!r})
+f = lambda *a, **k: oracle.mttkrp(*a, lib=lib, **k)
+g = lambda *a, **k: oracle.ttv(*a, lib=lib, **k)
+failed = []
+for c in P.MTTKRP_CHECKS:
+    try:
+        c(f, g)
+    except Exception as e:
+        failed.append(c.__name__)
+print("FAILED", len(failed), failed)
+"""
+
 RUNNER = r"""
 import sys
 sys.path.insert(0, {root!r}); sys.path.insert(0, {tests!r})
@@ -62,6 +89,21 @@ def test_pins_catch_mutant(name):
         open(msrc, "w").write(src.replace(old, new))
         lib = oracle.compile_library(msrc, os.path.join(td, "libmutant.so"))
         code = RUNNER.format(root=ROOT, tests=os.path.join(ROOT, "tests"), lib=lib)
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    caught = r.returncode != 0 or ("FAILED" in r.stdout and "FAILED 0 " not in r.stdout)
+    assert caught, f"mutant {name} survived every pin: {r.stdout} {r.stderr[-500:]}"
+
+
+@pytest.mark.parametrize("name", sorted(MTTKRP_MUTANTS))
+def test_mttkrp_pins_catch_mutant(name):
+    old, new = MTTKRP_MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique/found"
+    with tempfile.TemporaryDirectory() as td:
+        msrc = os.path.join(td, "mutant.c")
+        open(msrc, "w").write(src.replace(old, new))
+        lib = oracle.compile_library(msrc, os.path.join(td, "libmutant.so"))
+        code = RUNNER_MTTKRP.format(root=ROOT, tests=os.path.join(ROOT, "tests"), lib=lib)
         r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
     caught = r.returncode != 0 or ("FAILED" in r.stdout and "FAILED 0 " not in r.stdout)
     assert caught, f"mutant {name} survived every pin: {r.stdout} {r.stderr[-500:]}"

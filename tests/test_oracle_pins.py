@@ -64,3 +64,21 @@ def test_nonfinite_terms_follow_ieee_sum():
     vals = np.array([inf, 1.0, inf, -inf, nan, 2.0, -inf])
     s, v, _ = oracle.ttv(subs, vals, (4, 2), [1], [np.ones(2)])
     assert v[0] == inf and np.isnan(v[1]) and np.isnan(v[2]) and v[3] == -inf
+
+
+@pytest.mark.parametrize("check", P.MTTKRP_CHECKS, ids=lambda c: c.__name__)
+def test_mttkrp_pin(check):
+    check(oracle.mttkrp, oracle.ttv)
+
+
+def test_mttkrp_errors_and_empty():
+    subs = np.array([[0, 1], [1, 0]], dtype=np.int64)
+    vals = np.array([1.0, 2.0])
+    facs = [np.ones((2, 3)), np.ones((2, 3))]
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.mttkrp(np.array([[0, 2]]), np.array([1.0]), (2, 2), 0, facs)
+    assert e.value.code == -4
+    M = oracle.mttkrp(np.zeros((0, 2), np.int64), np.zeros(0), (2, 2), 1, facs)
+    assert M.shape == (2, 3) and not M.any()
+    M = oracle.mttkrp(subs, vals, (2, 2), 1, facs)
+    assert M.tolist() == [[2.0] * 3, [1.0] * 3]
