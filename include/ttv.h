@@ -288,6 +288,34 @@ int ttv_prepared_info(const ttv_prepared *p, int64_t *nnz_out, int32_t *order, s
 int ttv_prepared_workspace_size(const ttv_prepared *p, size_t *bytes);
 void ttv_prepared_free(ttv_prepared *p);
 
+/* ---- MTTKRP -------------------------------------------------------------------
+ * The matricized tensor times Khatri-Rao product, which the paper names as the
+ * kernel built on the sparse TTV (Sec. 3.3) and as future work (Sec. 5).
+ * Along mode n with factor matrices A_m (shape[m] x rank, row-major, binary64,
+ * device), m != n:
+ *     M(i, r) = sum over nonzeros k with subs[k, n] == i of
+ *               vals[k] * prod_{m != n, increasing} A_m(subs[k, m], r),
+ * so column r is the all-but-one TTV with the vectors A_m(:, r).  `out` is
+ * shape[n] x rank row-major binary64 on the device, written in full (rows no
+ * nonzero touches are 0).  Sums are formed in a fixed order: results are
+ * bit-identical run to run.  rank must be 1..TTV_MTTKRP_MAX_RANK.
+ *
+ * ttv_mttkrp_prepared runs on a tensor prepared (ttv_prepare) for every mode
+ * but n -- the layout sorts the nonzeros by subs[k, n] -- with one factor per
+ * prepared mode, in the order the modes were given to ttv_prepare; it is
+ * asynchronous on `stream` and takes `workspace` when it holds
+ * ttv_mttkrp_workspace_size bytes (else it allocates from the stream-ordered
+ * pool).  TTV_ERR_ARG for a tensor not prepared that way, a null factor or a
+ * bad rank.  ttv_mttkrp prepares, runs and releases in one call (factors:
+ * d pointers, factors[mode] is not read) and synchronises `stream`; errors
+ * as ttv_prepare. */
+#define TTV_MTTKRP_MAX_RANK 128
+int ttv_mttkrp_prepared(const ttv_prepared *p, const double *const *factors, int32_t rank, double *out,
+                        void *workspace, size_t workspace_bytes, ttv_stream_t stream);
+int ttv_mttkrp_workspace_size(const ttv_prepared *p, int32_t rank, size_t *bytes);
+int ttv_mttkrp(const ttv_tensor *t, int32_t mode, const double *const *factors, int32_t rank, double *out,
+               ttv_stream_t stream);
+
 /* ---- serving ------------------------------------------------------------------
  * A continuous-batching TTV server.  Registered tensors stay resident in
  * server-owned device memory.  Requests (contracted modes + host vectors)

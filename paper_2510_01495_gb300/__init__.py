@@ -329,6 +329,14 @@ def _declare_prep(lib):
     lib.ttv_prepared_workspace_size.restype = ctypes.c_int
     lib.ttv_prepared_free.argtypes = [ctypes.c_void_p]
     lib.ttv_prepared_free.restype = None
+    lib.ttv_mttkrp_prepared.argtypes = [ctypes.c_void_p, P(ctypes.c_void_p), ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    lib.ttv_mttkrp_prepared.restype = ctypes.c_int
+    lib.ttv_mttkrp_workspace_size.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_size_t)]
+    lib.ttv_mttkrp_workspace_size.restype = ctypes.c_int
+    lib.ttv_mttkrp.argtypes = [P(Tensor), ctypes.c_int32, P(ctypes.c_void_p), ctypes.c_int32, ctypes.c_void_p,
+                               ctypes.c_void_p]
+    lib.ttv_mttkrp.restype = ctypes.c_int
     lib._prep_declared = True
     return lib
 
@@ -400,6 +408,33 @@ class Prepared:
         finally:
             self._lib.ttv_out_free(ctypes.byref(res))
 
+    def mttkrp(self, factors, *, out=None, workspace=None, stream=None) -> torch.Tensor:
+        """MTTKRP along the one mode not prepared: ``factors`` are (shape[m],
+        rank) float64 CUDA matrices, one per prepared mode in their order."""
+        if self._h is None:
+            raise RuntimeError("prepared tensor released")
+        if len(factors) != len(self.modes):
+            raise ValueError("one factor per prepared mode")
+        rank = int(factors[0].shape[1])
+        for f, m in zip(factors, self.modes):
+            if (not f.is_cuda or f.dtype != torch.float64 or f.dim() != 2 or not f.is_contiguous()
+                    or f.shape != (self.shape[m], rank)):
+                raise ValueError("factors must be contiguous (shape[m], rank) float64 CUDA matrices")
+        n = [m for m in range(len(self.shape)) if m not in self.modes]
+        if len(n) != 1:
+            raise ValueError("MTTKRP needs a tensor prepared for every mode but one")
+        rows = self.shape[n[0]]
+        if out is None:
+            out = torch.empty((rows, rank), dtype=torch.float64, device=self.device)
+        if workspace is None:
+            nb = ctypes.c_size_t()
+            _check(self._lib, self._lib.ttv_mttkrp_workspace_size(self._h, rank, ctypes.byref(nb)))
+            workspace = torch.empty(max(1, nb.value), dtype=torch.uint8, device=self.device)
+        fp = (ctypes.c_void_p * len(factors))(*[f.data_ptr() for f in factors])
+        _check(self._lib, self._lib.ttv_mttkrp_prepared(self._h, fp, rank, out.data_ptr(), workspace.data_ptr(),
+                                                        workspace.numel(), _stream_handle(stream)))
+        return out
+
     def close(self):
         if self._h is not None:
             self._lib.ttv_prepared_free(self._h)
@@ -410,6 +445,20 @@ class Prepared:
             self.close()
         except Exception:
             pass
+
+
+def mttkrp(subs, vals, shape, mode: int, factors, stream=None) -> torch.Tensor:
+    """MTTKRP along ``mode`` (ttv_mttkrp): ``factors`` holds one (shape[m],
+    rank) float64 CUDA matrix per mode (the entry for ``mode`` is ignored)."""
+    lib = _declare_prep(load())
+    d = len(shape)
+    rank = int(next(f for m, f in enumerate(factors) if m != mode).shape[1])
+    fp = (ctypes.c_void_p * d)(*[0 if (m == mode or factors[m] is None) else factors[m].data_ptr()
+                                  for m in range(d)])
+    out = torch.empty((int(shape[mode]), rank), dtype=torch.float64, device=subs.device)
+    t = make_tensor(subs, vals, shape)
+    _check(lib, lib.ttv_mttkrp(ctypes.byref(t), int(mode), fp, rank, out.data_ptr(), _stream_handle(stream)))
+    return out
 
 
 # ---- autotuner ------------------------------------------------------------------

@@ -36,6 +36,13 @@ void launch_prep_keys(const StreamDesc& p, uint64_t* keys, double* idx, cudaStre
 void launch_prep_gather(const StreamDesc& p, const double* idx_sorted, void* vals_out, const PrepTerms& subs,
                         cudaStream_t stream);
 void launch_prep_count(const uint64_t* keys, int64_t n, unsigned long long* count, cudaStream_t stream);
+int64_t mttkrp_nchunks(int64_t n);
+size_t mttkrp_workspace_bytes(int64_t n, int32_t R);
+void launch_mttkrp_chunk_counts(const uint32_t* bits, int64_t n, uint32_t* counts, cudaStream_t stream);
+void launch_mttkrp(const void* vals, int val_f32, int n_v, const int32_t* const* subs, const double* const* factors,
+                   const uint32_t* bits, const uint64_t* row_keys, const uint32_t* chunk_base,
+                   const int32_t* next_head, int64_t n, int32_t R, int64_t rows, double* out, void* ws,
+                   cudaStream_t stream);
 void launch_reduce_by_key(const uint64_t* keys, const double* vals, int64_t n, void* state, const StreamDesc& p,
                           const SegOut& o, Status* st, cudaStream_t stream);
 
@@ -566,6 +573,8 @@ struct ttv_prepared {
     uint64_t* row_keys = nullptr;     // key of every result row
     void* vals = nullptr;             // values in key order
     int32_t* subs[TTV_MAX_D] = {nullptr};
+    uint32_t* chunk_base = nullptr;   // one surviving mode: heads before each 128-nonzero chunk (MTTKRP)
+    int32_t* next_head = nullptr;     // first chunk after c that holds a head (MTTKRP)
     size_t bytes = 0;
 };
 
@@ -1016,6 +1025,11 @@ int ttv_prepare(const ttv_tensor* t, const int32_t* modes, int32_t n_v, ttv_prep
     if (e != cudaSuccess) return drop(TTV_ERR_CUDA, "prepared tensor allocation");
     if (p0.nnz == 0) {
         e = cudaMalloc(&h->row_keys, 8);
+        if (e == cudaSuccess && p0.nr == 1) {
+            e = cudaMalloc(&h->chunk_base, 4);
+            if (e == cudaSuccess) e = cudaMemset(h->chunk_base, 0, 4);
+            if (e == cudaSuccess) e = cudaMalloc(&h->next_head, 4);
+        }
         if (e != cudaSuccess) return drop(TTV_ERR_CUDA, "prepared tensor allocation");
         *out = h;
         return TTV_OK;
@@ -1091,6 +1105,38 @@ int ttv_prepare(const ttv_tensor* t, const int32_t* modes, int32_t n_v, ttv_prep
     if (hs.err & kErrTimeout) return drop(fail(TTV_ERR_TIMEOUT, "a bounded device wait ran out"), "");
     if (hs.err) return drop(fail(TTV_ERR_CUDA, "internal device check failed"), "");
     h->nnz_out = (int64_t)hc;
+    if (p0.nr == 1) {
+        // MTTKRP chunk index: heads before every chunk (counted on the
+        // device, scanned here once)
+        const int64_t nc = mttkrp_nchunks(p0.nnz);
+        std::vector<uint32_t> hcnt((size_t)nc), base((size_t)nc + 1, 0);
+        uint32_t* dcnt = nullptr;
+        e = cudaMalloc(&h->chunk_base, ((size_t)nc + 1) * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&dcnt, (size_t)std::max<int64_t>(nc, 1) * 4);
+        if (e == cudaSuccess) {
+            launch_mttkrp_chunk_counts(h->head_bits, p0.nnz, dcnt, stream);
+            e = cudaMemcpyAsync(hcnt.data(), dcnt, (size_t)nc * 4, cudaMemcpyDeviceToHost, stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        }
+        if (e == cudaSuccess) {
+            for (int64_t c = 0; c < nc; ++c) base[(size_t)c + 1] = base[(size_t)c] + hcnt[(size_t)c];
+            e = cudaMemcpy(h->chunk_base, base.data(), ((size_t)nc + 1) * 4, cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess) {
+            std::vector<int32_t> nxt((size_t)std::max<int64_t>(nc, 1));
+            int32_t next = (int32_t)nc;
+            for (int64_t c = nc - 1; c >= 0; --c) {
+                nxt[(size_t)c] = next;
+                if (hcnt[(size_t)c] > 0) next = (int32_t)c;
+            }
+            e = cudaMalloc(&h->next_head, (size_t)std::max<int64_t>(nc, 1) * 4);
+            if (e == cudaSuccess) e = cudaMemcpy(h->next_head, nxt.data(), (size_t)std::max<int64_t>(nc, 1) * 4,
+                                                 cudaMemcpyHostToDevice);
+        }
+        if (dcnt) cudaFree(dcnt);
+        if (e != cudaSuccess) return drop(TTV_ERR_CUDA, "MTTKRP chunk index");
+        h->bytes += ((size_t)nc + 1) * 4 + (size_t)nc * 4;
+    }
     *out = h;
     return TTV_OK;
 }
@@ -1120,6 +1166,72 @@ int ttv_prepared_run(const ttv_prepared* h, const void* const* vecs, const int64
     return execute_prepared(h, vecs, v_dtype, out, o, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int ttv_mttkrp_workspace_size(const ttv_prepared* h, int32_t rank, size_t* bytes) {
+    if (!h || !bytes || rank < 1 || rank > TTV_MTTKRP_MAX_RANK) return fail(TTV_ERR_ARG, "bad MTTKRP arguments");
+    *bytes = mttkrp_workspace_bytes(h->nnz, rank);
+    return TTV_OK;
+}
+
+int ttv_mttkrp_prepared(const ttv_prepared* h, const double* const* factors, int32_t rank, double* out,
+                        void* workspace, size_t workspace_bytes, ttv_stream_t stream_) {
+    g_err.clear();
+    if (!h || !factors || !out) return fail(TTV_ERR_ARG, "null prepared tensor, factors or result");
+    if (rank < 1 || rank > TTV_MTTKRP_MAX_RANK) return fail(TTV_ERR_ARG, "rank %d outside 1..%d", rank, TTV_MTTKRP_MAX_RANK);
+    const StreamDesc& p0 = h->plan.desc;
+    if (p0.nr != 1 || !h->chunk_base)
+        return fail(TTV_ERR_ARG, "MTTKRP needs a tensor prepared for every mode but one");
+    const double* fac[TTV_MAX_D] = {nullptr};
+    for (int j = 0; j < h->n_v; ++j) {
+        fac[j] = factors[h->arg_of[j]];
+        if (!fac[j]) return fail(TTV_ERR_ARG, "null factor");
+    }
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    init_once();
+    const size_t need = mttkrp_workspace_bytes(h->nnz, rank);
+    void* ws = workspace;
+    bool own = false;
+    if (!ws || workspace_bytes < need) {
+        cudaError_t e = cudaMallocAsync(&ws, need, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "MTTKRP workspace");
+        own = true;
+    }
+    const int32_t* subs[TTV_MAX_D];
+    for (int j = 0; j < h->n_v; ++j) subs[j] = h->subs[j];
+    launch_mttkrp(h->vals, p0.val_f32, h->n_v, subs, fac, h->head_bits, h->row_keys, h->chunk_base, h->next_head,
+                  h->nnz, rank, p0.rshape[0], out, ws, stream);
+    if (own) cudaFreeAsync(ws, stream);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "MTTKRP launch");
+    return TTV_OK;
+}
+
+int ttv_mttkrp(const ttv_tensor* t, int32_t mode, const double* const* factors, int32_t rank, double* out,
+               ttv_stream_t stream) {
+    g_err.clear();
+    if (!t || !factors) return fail(TTV_ERR_ARG, "null tensor or factors");
+    if (t->d < 2 || t->d > TTV_MAX_D) return fail(TTV_ERR_ARG, "MTTKRP needs order 2..%d", TTV_MAX_D);
+    if (mode < 0 || mode >= t->d) return fail(TTV_ERR_MODE, "mode %d outside 0..%d", mode, t->d - 1);
+    int32_t modes[TTV_MAX_D];
+    const double* fac[TTV_MAX_D];
+    int n_v = 0;
+    for (int m = 0; m < t->d; ++m)
+        if (m != mode) {
+            modes[n_v] = m;
+            fac[n_v] = factors[m];
+            ++n_v;
+        }
+    ttv_prepared* h = nullptr;
+    int rc = ttv_prepare(t, modes, n_v, &h, stream);
+    if (rc != TTV_OK) return rc;
+    rc = ttv_mttkrp_prepared(h, fac, rank, out, nullptr, 0, stream);
+    if (rc == TTV_OK) {
+        const cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) rc = cuda_fail(e, "MTTKRP");
+    }
+    ttv_prepared_free(h);
+    return rc;
+}
+
 int ttv_prepared_info(const ttv_prepared* h, int64_t* nnz_out, int32_t* order, size_t* device_bytes) {
     if (!h) return fail(TTV_ERR_ARG, "null prepared tensor");
     if (nnz_out) *nnz_out = h->nnz_out;
@@ -1138,6 +1250,8 @@ void ttv_prepared_free(ttv_prepared* h) {
     if (!h) return;
     cudaDeviceSynchronize();
     if (h->head_bits) cudaFree(h->head_bits);
+    if (h->chunk_base) cudaFree(h->chunk_base);
+    if (h->next_head) cudaFree(h->next_head);
     if (h->row_keys) cudaFree(h->row_keys);
     if (h->vals) cudaFree(h->vals);
     for (int j = 0; j < TTV_MAX_D; ++j)
