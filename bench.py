@@ -298,6 +298,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="batch_512: skip the autotuner (planner rule only)")
     ap.add_argument("--prepared", action="store_true",
                     help="single workloads: prepare the tensor once (untimed), then time prepared runs")
+    ap.add_argument("--mttkrp", type=int, default=0, metavar="R",
+                    help="single workloads: time MTTKRP of rank R on the prepared tensor instead of the TTV")
     ap.add_argument("--ref-sample", type=int, default=1_000_000, help="largest per-step oracle sample")
     ap.add_argument("--ref-budget", type=float, default=90.0, help="seconds the reference arm's timed steps aim at")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -319,6 +321,8 @@ def main():
         return run_batch(args, rank, world, local_rank)
     if args.workload == "serve_64":
         return run_serve(args, rank, world, local_rank)
+    if args.mttkrp:
+        return run_mttkrp(args, rank, world, local_rank)
 
     import paper_2510_01495_gb300 as ttv
     torch.cuda.set_device(local_rank)
@@ -729,6 +733,143 @@ def run_serve(args, rank, world, local_rank):
                   "p99_ms": pst["p99_us"] / 1e3},
         "clocks": clk, "accuracy_fp32_storage": accuracy,
     }
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# FP64 multiply rate used as the MTTKRP roofline: the nominal FP64 rate of
+# 1.25 TFLOP/s counts a fused multiply-add as two flops, and a multiply
+# issues at the fused multiply-add rate, so 625 G multiplies/s.
+FP64_MUL_NOMINAL_G = 625.0
+
+
+def mttkrp_workload(problem):
+    """Output mode of the MTTKRP timed on a TTV workload: the surviving mode
+    of the all-but-one TTV, the contracted mode of the single TTV."""
+    d = problem.tensor.d
+    surv = [m for m in range(d) if m not in problem.modes]
+    mode = surv[0] if len(surv) == 1 else problem.modes[0]
+    return mode, [m for m in range(d) if m != mode]
+
+
+def run_mttkrp(args, rank, world, local_rank):
+    """MTTKRP of rank R, M(i,:) = sum of vals[k] * Hadamard product of the
+    factor rows A_m(subs[k,m], :) over the other modes, on the tensor prepared
+    once (untimed) for every mode but the output one; factors U[0,1)."""
+    import paper_2510_01495_gb300 as ttv
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = init_ranks(world, dev)
+    ttv.load()
+    wl = WORKLOADS[args.workload]
+    if wl["make"] is None:
+        raise SystemExit("--mttkrp applies to the single-tensor workloads")
+    R = int(args.mttkrp)
+    problem = wl["make"](dev, replica_seed(args.seed, rank), args.nnz)
+    t = problem.tensor
+    mode, others = mttkrp_workload(problem)
+    subs = t.subs.t().contiguous().t()
+    t_prep = time.perf_counter()
+    prep = ttv.Prepared(subs, t.vals, t.shape, others)
+    torch.cuda.synchronize(dev)
+    t_prep = time.perf_counter() - t_prep
+    g = torch.Generator(device=dev).manual_seed(replica_seed(args.seed, rank) + 77)
+    fd = [torch.rand((t.shape[m], R), dtype=torch.float64, device=dev, generator=g) for m in others]
+    out = torch.empty((t.shape[mode], R), dtype=torch.float64, device=dev)
+    nb = ctypes.c_size_t()
+    prep._lib.ttv_mttkrp_workspace_size(prep._h, R, ctypes.byref(nb))
+    ws = torch.empty(max(1, nb.value), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        prep.mttkrp(fd, out=out, workspace=ws, stream=stream)
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    ttv.profile_reset()
+    ttv.profile_enable(True)
+    barrier(dist)
+    torch.cuda.synchronize(dev)
+    launches0 = ttv.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        prep.mttkrp(fd, out=out, workspace=ws, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(dist)
+    launches = ttv.launch_count() - launches0
+    ms = max_over_ranks(dist, ev0.elapsed_time(ev1), dev)
+    ttv.profile_collect()
+    ttv.profile_enable(False)
+    clk = clocks.stop()
+    nnz, n_v = t.nnz, len(others)
+    per_kernel = {}
+    for name in ttv.profile_names():
+        tot, n = ttv.profile_get(name)
+        per_kernel[name] = {"ms_total": tot, "launches": n, "ms_avg": tot / max(1, n)}
+    dom_ms = per_kernel.get("mttkrp_chunks", {}).get("ms_avg")
+    muls = float(nnz) * R * n_v                     # factor products: n_v multiplies per nonzero and rank
+    achieved = muls / (dom_ms * 1e-3) / 1e9 if dom_ms else None
+    ms_step = ms / args.steps
+    line = {
+        "metric": "MTTKRP nonzeros/sec", "value": nnz * args.steps * world / (ms * 1e-3) / 1e9, "unit": "GNNZ/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"mttkrp_{args.workload}", "desc": wl["desc"], "rank": R, "mode": mode,
+                   "nnz": nnz, "rows": int(t.shape[mode]), "factors": "U[0,1) float64, row-major (shape[m], R)",
+                   "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "alu", "kernel": "mttkrp_chunks", "achieved": achieved, "peak": FP64_MUL_NOMINAL_G,
+                     "unit": "G FP64 mul/s", "frac": achieved / FP64_MUL_NOMINAL_G if achieved else None,
+                     "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s, fused multiply-add = 2 flops",
+                     "mul_per_launch": muls},
+        "step": {"gflops_f64": 2.0 * nnz * R * n_v / (ms_step * 1e-3) / 1e9},
+        "prepared": {"prepare_s": round(t_prep, 3), "device_bytes": prep.device_bytes},
+        "kernels": per_kernel, "gpu_launches": launches, "clocks": clk,
+    }
+    # end to end: host factors in, host result out, on the resident tensor
+    h_f = [f.cpu().pin_memory() for f in fd]
+    h_out = torch.empty(out.shape, dtype=torch.float64).pin_memory()
+    times = []
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for a, b in zip(fd, h_f):
+            a.copy_(b, non_blocking=True)
+        prep.mttkrp(fd, out=out, workspace=ws, stream=stream)
+        h_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        if i > 0:
+            times.append(time.perf_counter() - t0)
+    e2e_ms = max_over_ranks(dist, sum(times) / len(times) * 1e3, dev)
+    line["e2e"] = {"value": nnz * world / (e2e_ms * 1e-3) / 1e9, "unit": "GNNZ/s",
+                   "h2d_bytes_per_step": int(sum(f.numel() * 8 for f in h_f)),
+                   "d2h_bytes_per_step": int(h_out.numel() * 8), "ms_per_step": e2e_ms,
+                   "note": "resident prepared tensor; factors copied in and the result read back each step"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        hs, hv = t.subs.cpu().numpy(), t.vals.cpu().numpy()
+        hfac = [None] * t.d
+        for m, f in zip(others, h_f):
+            hfac[m] = f.numpy()
+        hfac[mode] = np.zeros((t.shape[mode], R))
+        m = min(nnz, 100_000)
+        t0 = time.perf_counter()
+        oracle.mttkrp(hs[:m], hv[:m], t.shape, mode, hfac)
+        dt = time.perf_counter() - t0
+        m2 = int(min(nnz, max(m, m * 10.0 / max(dt, 1e-6))))
+        t0 = time.perf_counter()
+        oracle.mttkrp(hs[:m2], hv[:m2], t.shape, mode, hfac)
+        dt2 = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": m2 / dt2 / 1e9, "unit": "GNNZ/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {m2} of {nnz} nonzeros, rank {R}, one call, {dt2:.1f} s"}
+    prep.close()
     if dist:
         dist.destroy_process_group()
     if rank == 0:
