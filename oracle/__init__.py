@@ -1,12 +1,13 @@
-"""CPU oracle for the sparse tensor-times-vector product (paper Sec. 3.3, Eq. 3)
-and for the MTTKRP built on it (named in Sec. 3.3 and Sec. 5).
+"""CPU oracle for the sparse tensor-times-vector product (paper Sec. 3.3, Eq. 3),
+the MTTKRP built on it (named in Sec. 3.3 and Sec. 5), and the paper's two
+simple kernels, the dense dot product (Eq. 1) and matrix-vector product (Eq. 2).
 
 TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it; the CUDA
 library (``paper_2510_01495_gb300``) neither imports nor links it, and this
 package imports nothing from the library.
 
-``ttv`` and ``mttkrp`` wrap the plain C statements in ``ttv_oracle.c``
+``ttv``, ``mttkrp``, ``dot`` and ``matvec`` wrap the plain C statements in ``ttv_oracle.c``
 (built with gcc and ``-ffp-contract=off``).  It upcasts float32 inputs to float64 exactly before
 the call, so an FP32-stored tensor is evaluated as the exact FP64 values it
 holds.  Parity status of every function here: pinned (see tests/test_oracle_pins.py).
@@ -90,6 +91,12 @@ def load_library(path: str):
         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
         ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
         ctypes.POINTER(ctypes.c_double)]
+    lib.oracle_dot.restype = ctypes.c_int
+    lib.oracle_dot.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)]
+    lib.oracle_matvec.restype = ctypes.c_int
+    lib.oracle_matvec.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                                  ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     return lib
 
 
@@ -203,3 +210,43 @@ def mttkrp(subs, vals, shape, mode: int, factors, lib=None) -> np.ndarray:
     if rc != 0:
         raise OracleError(rc)
     return out
+
+
+def dot(x, y, lib=None) -> float:
+    """x . y by the plain definition (Eq. 1): rounded products summed in index
+    order with Neumaier's compensation."""
+    lib = lib or _get_lib()
+    x = _as_f64(x).reshape(-1)
+    y = _as_f64(y).reshape(-1)
+    if x.size != y.size:
+        raise ValueError("vectors of different lengths")
+    out = ctypes.c_double()
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib.oracle_dot(int(x.size), x.ctypes.data_as(dp), y.ctypes.data_as(dp), ctypes.byref(out))
+    if rc != 0:
+        raise OracleError(rc)
+    return float(out.value)
+
+
+def matvec(A, x, lib=None) -> np.ndarray:
+    """A x by the plain definition (Eq. 2): row i is the dot product of A's row
+    i with x.  ``A`` is read in its own memory order (C or Fortran)."""
+    lib = lib or _get_lib()
+    A = np.asarray(A)
+    if A.ndim != 2:
+        raise ValueError("A must be a matrix")
+    if A.dtype != np.float64:
+        A = _as_f64(A)
+    n1, n2 = A.shape
+    x = _as_f64(x).reshape(-1)
+    if x.size != n2:
+        raise ValueError("x length differs from the number of columns")
+    if A.strides[0] % 8 or A.strides[1] % 8:
+        A = np.ascontiguousarray(A)
+    y = np.zeros(n1, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib.oracle_matvec(n1, n2, A.ctypes.data_as(dp), A.strides[0] // 8, A.strides[1] // 8,
+                           x.ctypes.data_as(dp), y.ctypes.data_as(dp))
+    if rc != 0:
+        raise OracleError(rc)
+    return y

@@ -38,6 +38,9 @@
  * rational arithmetic, d = 1 (dot product, Eq. 1) and d = 2 (matrix-vector
  * product, Eq. 2) special cases, all-ones vector = mode sum, linearity, the
  * all-modes multilinear form, mode-order independence, distinct-tuple counts.
+ * The dense dot and matrix-vector statements at the end are pinned to exact
+ * rational sums, closed forms, the d = 1 and d = 2 TTV bit for bit, and
+ * storage-order independence.
  */
 #define _GNU_SOURCE
 #include <stdint.h>
@@ -283,5 +286,48 @@ int oracle_mttkrp(int32_t d, const int64_t *shape, int64_t nnz, const int64_t *s
     for (int64_t q = 0; q < rows * rank; ++q)
         if (isfinite(out[q])) out[q] += comp[q];
     free(comp);
+    return ORACLE_OK;
+}
+
+/*
+ * Dense vector dot product (paper Sec. 3.1, Eq. 1) and dense matrix-vector
+ * product (paper Sec. 3.2, Eq. 2), the paper's two simple kernels, by their
+ * plain definitions:
+ *
+ *     x . y = sum_{i=0}^{n-1} x[i] * y[i]
+ *     y[i]  = sum_{j=0}^{n2-1} A(i, j) * x[j],   i = 0 .. n1-1
+ *
+ * Each product is rounded to binary64, and each sum runs over increasing i
+ * (dot) or j (matrix row) with Neumaier's compensated summation, as the TTV
+ * groups above; a non-finite running sum is returned as the plain IEEE sum.
+ * A(i, j) is A[i * stride_row + j * stride_col], so row-major ("C") storage
+ * has strides (n2, 1) and pyttb's column-major ("F") storage (1, n1).
+ */
+static double neumaier_sum_products(const double *a, int64_t sa, const double *b, int64_t n)
+{
+    double sum = 0.0, comp = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double t = a[i * sa] * b[i];
+        const double s = sum + t;
+        if (fabs(sum) >= fabs(t)) comp += (sum - s) + t;
+        else                      comp += (t - s) + sum;
+        sum = s;
+    }
+    return isfinite(sum) ? sum + comp : sum;
+}
+
+int oracle_dot(int64_t n, const double *x, const double *y, double *out)
+{
+    if (n < 0 || !out || (n > 0 && (!x || !y))) return ORACLE_ERR_ARG;
+    *out = neumaier_sum_products(x, 1, y, n);
+    return ORACLE_OK;
+}
+
+int oracle_matvec(int64_t n1, int64_t n2, const double *A, int64_t stride_row, int64_t stride_col,
+                  const double *x, double *y)
+{
+    if (n1 < 0 || n2 < 0 || (n1 > 0 && !y) || (n1 > 0 && n2 > 0 && (!A || !x))) return ORACLE_ERR_ARG;
+    for (int64_t i = 0; i < n1; ++i)
+        y[i] = neumaier_sum_products(A + i * stride_row, stride_col, x, n2);
     return ORACLE_OK;
 }

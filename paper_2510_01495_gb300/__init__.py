@@ -188,6 +188,18 @@ class Result:
     def __iter__(self):
         return iter((self.subs, self.vals, self.shape))
 
+    def to_sptensor_arrays(self):
+        """Host arrays in pyttb's sptensor layout: ``subs`` (nnz, order) int64,
+        ``vals`` (nnz, 1) float64 and the shape.  A dense result is returned
+        as its nonzero cells in the same row-major order."""
+        if self.is_dense:
+            flat = self.vals.reshape(-1)
+            idx = torch.nonzero(flat, as_tuple=False).reshape(-1)
+            subs = torch.stack(torch.unravel_index(idx, self.shape), dim=1) if self.shape else \
+                torch.zeros((idx.numel(), 0), dtype=torch.int64, device=flat.device)
+            return subs.cpu().numpy(), flat[idx].reshape(-1, 1).cpu().numpy(), self.shape
+        return self.subs.cpu().numpy(), self.vals.reshape(-1, 1).cpu().numpy(), self.shape
+
 
 def ttv_multi(subs: torch.Tensor, vals: torch.Tensor, shape, modes, vecs, *, fmt="sparse", path="auto",
               accum="fp64", deterministic=False, out_subs: torch.Tensor | None = None,
@@ -255,6 +267,50 @@ def ttv_multi(subs: torch.Tensor, vals: torch.Tensor, shape, modes, vecs, *, fmt
 def ttv_single(subs, vals, shape, mode: int, v: torch.Tensor, **kw) -> Result:
     """TTV with one vector along ``mode`` (paper Eq. 3)."""
     return ttv_multi(subs, vals, shape, [mode], [v], **kw)
+
+
+def resolve_dims(d: int, nvec: int, dims=None, exclude_dims=None):
+    """pyttb's mode specification for ttv: ``dims`` lists the modes to
+    contract, ``exclude_dims`` the modes to keep (never both); neither means
+    every mode.  Returns the modes in increasing order and, for each, the
+    index of its vector: with one vector per tensor mode (nvec == d) mode m
+    takes vectors[m]; otherwise there is one vector per listed mode, paired
+    with the modes in the order they were listed."""
+    if dims is not None and exclude_dims is not None:
+        raise ValueError("give dims or exclude_dims, not both")
+    if dims is None and exclude_dims is None:
+        listed = list(range(d))
+    elif exclude_dims is not None:
+        ex = [exclude_dims] if isinstance(exclude_dims, int) else [int(m) for m in exclude_dims]
+        if any(m < 0 or m >= d for m in ex) or len(set(ex)) != len(ex):
+            raise ValueError(f"exclude_dims {ex} invalid for a {d}-way tensor")
+        listed = [m for m in range(d) if m not in ex]
+    else:
+        listed = [dims] if isinstance(dims, int) else [int(m) for m in dims]
+    if any(m < 0 or m >= d for m in listed) or len(set(listed)) != len(listed):
+        raise ValueError(f"modes {listed} invalid for a {d}-way tensor")
+    order = sorted(range(len(listed)), key=lambda j: listed[j])
+    modes = [listed[j] for j in order]
+    if nvec > d:
+        raise ValueError(f"{nvec} vectors for a {d}-way tensor")
+    if nvec == d:
+        return modes, list(modes)
+    if nvec != len(listed):
+        raise ValueError(f"{nvec} vectors for {len(listed)} modes")
+    return modes, order
+
+
+def ttv(subs, vals, shape, vectors, dims=None, exclude_dims=None, *, fmt="auto", **kw):
+    """TTV with pyttb's calling convention (sptensor.ttv): ``vectors`` is one
+    vector or a list, the modes come from ``dims`` / ``exclude_dims`` (see
+    ``resolve_dims``), the result is dense when more than half its cells are
+    nonzero (``fmt="auto"``), and an order-0 result is returned as a float."""
+    vecs = [vectors] if isinstance(vectors, torch.Tensor) else list(vectors)
+    modes, vidx = resolve_dims(len(shape), len(vecs), dims, exclude_dims)
+    r = ttv_multi(subs, vals, shape, modes, [vecs[i] for i in vidx], fmt=fmt, **kw)
+    if r.shape == ():
+        return float(r.vals.reshape(-1)[0])
+    return r
 
 
 # ---- measurement hooks (per-kernel CUDA-event timing, launch counts) --------

@@ -370,3 +370,96 @@ def check_mttkrp_bruteforce_rounded(mttkrp, ttv=None):
 
 
 MTTKRP_CHECKS = [check_mttkrp_equals_ttv_columns, check_mttkrp_bruteforce_exact, check_mttkrp_bruteforce_rounded]
+
+
+# ---- dense dot product (Eq. 1) and matrix-vector product (Eq. 2) --------------------
+
+def _dyadic(g, size):
+    return g.integers(-16, 17, size=size).astype(np.float64) / 16.0
+
+
+def check_dot_exact_dyadic(dot, matvec=None, ttv=None):
+    """Sums of exactly representable products with exact partial sums: the
+    result is the exact rational value."""
+    for seed in range(40):
+        g = rng(7000 + seed)
+        n = int(g.integers(0, 300))
+        x, y = _dyadic(g, n), _dyadic(g, n)
+        want = sum((Fraction(float(a)) * Fraction(float(b)) for a, b in zip(x, y)), Fraction(0))
+        assert Fraction(dot(x, y)) == want, seed
+
+
+def check_dot_rounded_bound(dot, matvec=None, ttv=None):
+    """Random doubles: within one rounding per product plus the compensated
+    sum's bound of the exact value."""
+    for seed in range(40):
+        g = rng(7100 + seed)
+        n = int(g.integers(1, 400))
+        x, y = g.uniform(-1, 1, n), g.uniform(-1, 1, n)
+        exact = sum((Fraction(float(a)) * Fraction(float(b)) for a, b in zip(x, y)), Fraction(0))
+        A = float(np.sum(np.abs(x) * np.abs(y)))
+        bound = EPS * A * (1 + 1e-9) + 2 * EPS * abs(float(exact))
+        assert abs(Fraction(dot(x, y)) - exact) <= Fraction(bound), seed
+
+
+def check_dot_closed_forms(dot, matvec=None, ttv=None):
+    """sum i = n(n-1)/2 and sum i^2 = (n-1)n(2n-1)/6 (exact in binary64 here)."""
+    for n in (1, 2, 7, 1000, 100_000):
+        i = np.arange(n, dtype=np.float64)
+        assert dot(i, np.ones(n)) == n * (n - 1) // 2
+        assert dot(i, i) == (n - 1) * n * (2 * n - 1) // 6
+    assert dot(np.zeros(0), np.zeros(0)) == 0.0
+
+
+def check_dot_is_order0_ttv(dot, matvec=None, ttv=None):
+    """Eq. 1 is Eq. 3 with d = 1 and the one mode contracted: the vector x as a
+    1-way COO tensor (subscripts 0..n-1 in order) times y, same products and
+    same summation order, so equal bit for bit."""
+    for seed in range(20):
+        g = rng(7200 + seed)
+        n = int(g.integers(1, 500))
+        x, y = g.uniform(0, 1, n), g.uniform(-1, 1, n)
+        _, v, sh = ttv(np.arange(n, dtype=np.int64).reshape(n, 1), x, (n,), [0], [y])
+        assert sh == () and v[0] == dot(x, y), seed
+
+
+def check_matvec_rows_are_dots(dot, matvec, ttv=None):
+    """Row i of A x is the dot product of row i with x, bit for bit, whatever
+    the storage order of A."""
+    for seed in range(20):
+        g = rng(7300 + seed)
+        n1, n2 = int(g.integers(1, 40)), int(g.integers(1, 40))
+        A = g.uniform(-1, 1, (n1, n2))
+        x = g.uniform(-1, 1, n2)
+        want = np.array([dot(np.ascontiguousarray(A[i]), x) for i in range(n1)])
+        for M in (A, np.asfortranarray(A), np.ascontiguousarray(A.T).T):
+            assert np.array_equal(matvec(M, x), want), seed
+
+
+def check_matvec_is_mode1_ttv(dot, matvec, ttv):
+    """Eq. 2 is Eq. 3 with d = 2 contracted along the second mode: the dense
+    matrix as a COO tensor listed row by row gives the same groups in the same
+    order, so the same bits."""
+    for seed in range(20):
+        g = rng(7400 + seed)
+        n1, n2 = int(g.integers(1, 30)), int(g.integers(1, 30))
+        A = g.uniform(0, 1, (n1, n2))
+        x = g.uniform(0, 1, n2)
+        subs = np.array([[i, j] for i in range(n1) for j in range(n2)], dtype=np.int64)
+        _, v, sh = ttv(subs, A.reshape(-1), (n1, n2), [1], [x], dense=True)
+        assert sh == (n1,) and np.array_equal(v, matvec(A, x)), seed
+
+
+def check_matvec_exact_dyadic(dot, matvec, ttv=None):
+    for seed in range(20):
+        g = rng(7500 + seed)
+        n1, n2 = int(g.integers(1, 25)), int(g.integers(1, 25))
+        A, x = _dyadic(g, (n1, n2)), _dyadic(g, n2)
+        y = matvec(np.asfortranarray(A), x)
+        for i in range(n1):
+            want = sum((Fraction(float(A[i, j])) * Fraction(float(x[j])) for j in range(n2)), Fraction(0))
+            assert Fraction(float(y[i])) == want, (seed, i)
+
+
+DENSE_CHECKS = [check_dot_exact_dyadic, check_dot_rounded_bound, check_dot_closed_forms, check_dot_is_order0_ttv,
+                check_matvec_rows_are_dots, check_matvec_is_mode1_ttv, check_matvec_exact_dyadic]

@@ -47,6 +47,34 @@ MTTKRP_MUTANTS = {
                                ""),
 }
 
+DENSE_MUTANTS = {
+    "dense_shifted_index": ("const double t = a[i * sa] * b[i];",
+                            "const double t = a[i * sa] * b[i + 1 < n ? i + 1 : i];"),
+    "dense_no_compensation": ("if (fabs(sum) >= fabs(t)) comp += (sum - s) + t;\n        else                      comp += (t - s) + sum;",
+                              ""),
+    "matvec_transposed": ("y[i] = neumaier_sum_products(A + i * stride_row, stride_col, x, n2);",
+                          "y[i] = neumaier_sum_products(A + (i % n2) * stride_col, stride_row, x, n2 < n1 ? n2 : n1);"),
+    "matvec_skips_last_column": ("y[i] = neumaier_sum_products(A + i * stride_row, stride_col, x, n2);",
+                                 "y[i] = neumaier_sum_products(A + i * stride_row, stride_col, x, n2 > 1 ? n2 - 1 : n2);"),
+}
+
+RUNNER_DENSE = r"""
+import sys
+sys.path.insert(0, {root!r}); sys.path.insert(0, {tests!r})
+import oracle, oracle_pins as P
+lib = oracle.load_library({lib!r})
+dot = lambda *a, **k: oracle.dot(*a, lib=lib, **k)
+mv = lambda *a, **k: oracle.matvec(*a, lib=lib, **k)
+g = lambda *a, **k: oracle.ttv(*a, lib=lib, **k)
+failed = []
+for c in P.DENSE_CHECKS:
+    try:
+        c(dot, mv, g)
+    except Exception as e:
+        failed.append(c.__name__)
+print("FAILED", len(failed), failed)
+"""
+
 RUNNER_MTTKRP = r"""
 import sys
 sys.path.insert(0, {root!r}); sys.path.insert(0, {tests!r})
@@ -104,6 +132,21 @@ def test_mttkrp_pins_catch_mutant(name):
         open(msrc, "w").write(src.replace(old, new))
         lib = oracle.compile_library(msrc, os.path.join(td, "libmutant.so"))
         code = RUNNER_MTTKRP.format(root=ROOT, tests=os.path.join(ROOT, "tests"), lib=lib)
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    caught = r.returncode != 0 or ("FAILED" in r.stdout and "FAILED 0 " not in r.stdout)
+    assert caught, f"mutant {name} survived every pin: {r.stdout} {r.stderr[-500:]}"
+
+
+@pytest.mark.parametrize("name", sorted(DENSE_MUTANTS))
+def test_dense_pins_catch_mutant(name):
+    old, new = DENSE_MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique/found"
+    with tempfile.TemporaryDirectory() as td:
+        msrc = os.path.join(td, "mutant.c")
+        open(msrc, "w").write(src.replace(old, new))
+        lib = oracle.compile_library(msrc, os.path.join(td, "libmutant.so"))
+        code = RUNNER_DENSE.format(root=ROOT, tests=os.path.join(ROOT, "tests"), lib=lib)
         r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
     caught = r.returncode != 0 or ("FAILED" in r.stdout and "FAILED 0 " not in r.stdout)
     assert caught, f"mutant {name} survived every pin: {r.stdout} {r.stderr[-500:]}"

@@ -82,3 +82,18 @@ def test_mttkrp_errors_and_empty():
     assert M.shape == (2, 3) and not M.any()
     M = oracle.mttkrp(subs, vals, (2, 2), 1, facs)
     assert M.tolist() == [[2.0] * 3, [1.0] * 3]
+
+
+@pytest.mark.parametrize("check", P.DENSE_CHECKS, ids=lambda c: c.__name__)
+def test_dense_kernel_pin(check):
+    check(oracle.dot, oracle.matvec, oracle.ttv)
+
+
+def test_dense_kernels_errors_and_empty():
+    with pytest.raises(ValueError):
+        oracle.dot(np.ones(3), np.ones(4))
+    with pytest.raises(ValueError):
+        oracle.matvec(np.ones((2, 3)), np.ones(2))
+    assert oracle.dot(np.zeros(0), np.zeros(0)) == 0.0
+    assert oracle.matvec(np.zeros((3, 0)), np.zeros(0)).tolist() == [0.0, 0.0, 0.0]
+    assert oracle.matvec(np.zeros((0, 4)), np.ones(4)).shape == (0,)
