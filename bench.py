@@ -46,6 +46,10 @@ WORKLOADS = {
         desc="512 independent 3-to-5-way COO tensors, nnz log-uniform [1e3, 2e6], sizes U[50, 50000], own mode each, one graph launch"),
     "serve_64": dict(make=None, fmt="sparse",
         desc="Poisson TTV requests against 64 resident 4-way FP32 tensors (nnz log-uniform [1e4, 5e7]), random mode, fresh vectors"),
+    "dot_1e8": dict(make=None, fmt=None,
+        desc="dense dot product (Eq. 1) of two float64 vectors of 1e8 elements, U[0,1)"),
+    "matvec_1e4": dict(make=None, fmt=None,
+        desc="dense matrix-vector product (Eq. 2), float64 10000x10000 matrix (--order C or F), U[0,1)"),
     "single_3way_100": dict(
         make=lambda dev, seed, nnz=None: S.single_3way_100(seed=seed, device=dev), fmt="sparse",
         desc="single TTV mode 0 of a 100^3 COO tensor, nnz 1e4 uniform distinct, sparse 100x100 result"),
@@ -248,6 +252,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
+    if wl["make"] is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm covers the single-tensor TTV "
+                          f"workloads, not {args.workload}"}), flush=True)
+        return
     problem = wl["make"]("cpu", args.seed, args.nnz)
     import oracle
     oracle.build()
@@ -298,6 +306,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="batch_512: skip the autotuner (planner rule only)")
     ap.add_argument("--prepared", action="store_true",
                     help="single workloads: prepare the tensor once (untimed), then time prepared runs")
+    ap.add_argument("--order", default="F", choices=["C", "F"], help="matvec_1e4: matrix storage order")
     ap.add_argument("--mttkrp", type=int, default=0, metavar="R",
                     help="single workloads: time MTTKRP of rank R on the prepared tensor instead of the TTV")
     ap.add_argument("--ref-sample", type=int, default=1_000_000, help="largest per-step oracle sample")
@@ -310,7 +319,7 @@ def main():
     args = ap.parse_args()
     if args.seed == 0:
         args.seed = {"allbutone_4way_1000": 2, "single_5way_zipf": 3, "single_3way_100": 1, "batch_512": 5,
-                     "serve_64": 6}[args.workload]
+                     "serve_64": 6, "dot_1e8": 8, "matvec_1e4": 9}[args.workload]
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -323,6 +332,8 @@ def main():
         return run_serve(args, rank, world, local_rank)
     if args.mttkrp:
         return run_mttkrp(args, rank, world, local_rank)
+    if args.workload in ("dot_1e8", "matvec_1e4"):
+        return run_dense(args, rank, world, local_rank)
 
     import paper_2510_01495_gb300 as ttv
     torch.cuda.set_device(local_rank)
@@ -870,6 +881,148 @@ def run_mttkrp(args, rank, world, local_rank):
         line["cpu_baseline"] = {"value": m2 / dt2 / 1e9, "unit": "GNNZ/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {m2} of {nnz} nonzeros, rank {R}, one call, {dt2:.1f} s"}
     prep.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_dense(args, rank, world, local_rank):
+    """The paper's two simple kernels: one ttv_dot (1e8 elements) or one
+    ttv_matvec (10000 x 10000) per step through the C ABI, operands resident;
+    elements/s with the HBM roofline of the kernel."""
+    import paper_2510_01495_gb300 as ttv
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = init_ranks(world, dev)
+    lib = ttv._declare_dense(ttv.load())
+    seed = replica_seed(args.seed, rank)
+    stream = torch.cuda.current_stream(dev)
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    if args.workload == "dot_1e8":
+        n = args.nnz or 100_000_000
+        x = S.uniform(seed, 1, n, device=dev)
+        y = S.uniform(seed, 2, n, device=dev)
+        out = torch.empty(1, dtype=torch.float64, device=dev)
+        ws = torch.empty(max(1, ttv.dot_workspace_size(n)), dtype=torch.uint8, device=dev)
+        elems, alg_bytes = n, 16 * n + 8
+        kernel = "dot"
+
+        def call():
+            rc = lib.ttv_dot(x.data_ptr(), y.data_ptr(), n, 0, out.data_ptr(), ws.data_ptr(), ws.numel(), sh)
+            if rc:
+                raise ttv.TTVError(rc, lib.ttv_last_error().decode())
+        host_in = [x, y]
+        res = out
+        cfg = {"n": n}
+    else:
+        n1 = n2 = 10_000
+        A = S.uniform(seed, 1, n1 * n2, device=dev).reshape(n1, n2)
+        if args.order == "F":
+            A = A.t().contiguous().t()
+        x = S.uniform(seed, 2, n2, device=dev)
+        out = torch.empty(n1, dtype=torch.float64, device=dev)
+        ws = torch.empty(max(1, ttv.matvec_workspace_size(A)), dtype=torch.uint8, device=dev)
+        elems, alg_bytes = n1 * n2, 8 * n1 * n2 + 8 * n2 + 8 * n1
+        kernel = "matvec"
+        sr, sc = A.stride(0), A.stride(1)
+
+        def call():
+            rc = lib.ttv_matvec(A.data_ptr(), n1, n2, sr, sc, 0, x.data_ptr(), out.data_ptr(), ws.data_ptr(),
+                                ws.numel(), sh)
+            if rc:
+                raise ttv.TTVError(rc, lib.ttv_last_error().decode())
+        host_in = [A, x]
+        res = out
+        cfg = {"n1": n1, "n2": n2, "order": args.order}
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    ttv.profile_reset()
+    ttv.profile_enable(True)
+    barrier(dist)
+    torch.cuda.synchronize(dev)
+    launches0 = ttv.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        call()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(dist)
+    launches = ttv.launch_count() - launches0
+    ms = max_over_ranks(dist, ev0.elapsed_time(ev1), dev)
+    ttv.profile_collect()
+    ttv.profile_enable(False)
+    clk = clocks.stop()
+    per_kernel = {}
+    for name in ttv.profile_names():
+        tot, cnt = ttv.profile_get(name)
+        per_kernel[name] = {"ms_total": tot, "launches": cnt, "ms_avg": tot / max(1, cnt)}
+    peaks, peak_src = load_peaks()
+    peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    dom_ms = per_kernel.get(kernel, {}).get("ms_avg")
+    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms else None
+    ms_step = ms / args.steps
+    line = {
+        "metric": "dense elements/sec", "value": elems * args.steps * world / (ms * 1e-3) / 1e9, "unit": "Gelem/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload=args.workload, desc=WORKLOADS[args.workload]["desc"],
+                       l2="inputs larger than L2 (no flush)",
+                       parallelism=f"{world} independent replicas" if world > 1 else "1 GPU", **cfg),
+        "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "peak_source": f"{peak_src} hbm_gbs", "alg_bytes_per_launch": alg_bytes,
+                     "fp64_fma_cap_gbs": (16.0 if kernel == "dot" else 8.0) * FP64_MUL_NOMINAL_G},
+        "kernels": per_kernel, "gpu_launches": launches, "clocks": clk,
+    }
+    # end to end: operands copied in from pinned host memory, the result read back
+    h_in = [t.cpu().pin_memory() for t in host_in]
+    d_in = [torch.empty_strided(t.shape, t.stride(), dtype=t.dtype, device=dev) for t in host_in]
+    h_out = torch.empty(res.shape, dtype=torch.float64).pin_memory()
+    times = []
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for a, b in zip(d_in, h_in):
+            a.copy_(b, non_blocking=True)
+        if kernel == "dot":
+            ttv.dot(d_in[0], d_in[1], out=out, workspace=ws, stream=stream)
+        else:
+            ttv.matvec(d_in[0], d_in[1], out=out, workspace=ws, stream=stream)
+        h_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        if i > 0:
+            times.append(time.perf_counter() - t0)
+    e2e_ms = max_over_ranks(dist, sum(times) / len(times) * 1e3, dev)
+    line["e2e"] = {"value": elems * world / (e2e_ms * 1e-3) / 1e9, "unit": "Gelem/s",
+                   "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in h_in)),
+                   "d2h_bytes_per_step": int(h_out.numel() * 8), "ms_per_step": e2e_ms}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        if kernel == "dot":
+            m = min(n, 20_000_000)
+            xs, ys = h_in[0][:m].numpy(), h_in[1][:m].numpy()
+            t0 = time.perf_counter()
+            oracle.dot(xs, ys)
+            dt = time.perf_counter() - t0
+            sample = f"first {m} of {n} elements, one call, {dt:.2f} s"
+        else:
+            rows = 2000
+            Ah = h_in[0][:rows].numpy()
+            t0 = time.perf_counter()
+            oracle.matvec(Ah, h_in[1].numpy())
+            dt = time.perf_counter() - t0
+            m = rows * 10_000
+            sample = f"first {rows} of 10000 rows ({args.order} order), one call, {dt:.2f} s"
+        line["cpu_baseline"] = {"value": m / dt / 1e9, "unit": "Gelem/s", "cores": 1, "kind": "oracle",
+                                "sample": sample}
     if dist:
         dist.destroy_process_group()
     if rank == 0:

@@ -66,7 +66,14 @@ typedef enum {
     TTV_OUT_SPARSE = 0,          /* canonical COO (default)                          */
     TTV_OUT_DENSE = 1,           /* dense row-major array over shape[R]              */
     TTV_OUT_AUTO = 2             /* dense when nnz_out > 0.5 * prod(shape[R]): the
-                                    pyttb conversion rule the paper mentions (Sec. 3.3) */
+                                    pyttb conversion rule the paper mentions (Sec. 3.3).
+                                    Computed sparse, converted when the result is
+                                    finalised (end of a synchronous call, or
+                                    ttv_out_sync): a library-allocated result moves
+                                    to a new dense buffer; caller buffers are
+                                    converted in place when vals_capacity holds every
+                                    cell, else the result stays sparse.  is_dense and
+                                    nnz report the outcome. */
 } ttv_out_format;
 
 typedef enum {
@@ -315,6 +322,30 @@ int ttv_mttkrp_prepared(const ttv_prepared *p, const double *const *factors, int
 int ttv_mttkrp_workspace_size(const ttv_prepared *p, int32_t rank, size_t *bytes);
 int ttv_mttkrp(const ttv_tensor *t, int32_t mode, const double *const *factors, int32_t rank, double *out,
                ttv_stream_t stream);
+
+/* ---- the paper's two simple kernels on dense operands ---------------------------
+ * ttv_dot: x . y = sum_{i<n} x[i] * y[i] (paper Sec. 3.1, Eq. 1).  x and y are
+ * device arrays of n elements of `dtype` (float64 or float32, both the same;
+ * float32 is upcast exactly); *out (device) receives the binary64 result.
+ * ttv_matvec: y[i] = sum_{j<n2} A(i, j) * x[j], i < n1 (paper Sec. 3.2, Eq. 2),
+ * with A(i, j) = A[i * stride_row + j * stride_col] (elements): row-major
+ * storage has strides (n2, 1), pyttb's column-major storage (1, n1).  One of
+ * the strides must be 1 (or the matrix a single row or column), else
+ * TTV_ERR_UNSUPPORTED.  A and x are `dtype`, y (device, n1 doubles) binary64.
+ * n1 or n2 == 0 gives y = 0 (n1 == 0: nothing written).
+ *
+ * Both are asynchronous on `stream`.  Each element costs one binary64 fused
+ * multiply-add; the combination across lanes, CTAs and column chunks is in
+ * a fixed order, so results are bit-identical from run to run (they differ
+ * from a sequential sum by rounding only).  `workspace` is used when it holds
+ * the *_workspace_size bytes, else scratch comes from the stream-ordered
+ * pool.  Errors: TTV_ERR_ARG for a null pointer or a negative size. */
+int ttv_dot(const void *x, const void *y, int64_t n, ttv_dtype dtype, double *out, void *workspace,
+            size_t workspace_bytes, ttv_stream_t stream);
+int ttv_dot_workspace_size(int64_t n, size_t *bytes);
+int ttv_matvec(const void *A, int64_t n1, int64_t n2, int64_t stride_row, int64_t stride_col, ttv_dtype dtype,
+               const void *x, double *y, void *workspace, size_t workspace_bytes, ttv_stream_t stream);
+int ttv_matvec_workspace_size(int64_t n1, int64_t n2, int64_t stride_row, int64_t stride_col, size_t *bytes);
 
 /* ---- serving ------------------------------------------------------------------
  * A continuous-batching TTV server.  Registered tensors stay resident in

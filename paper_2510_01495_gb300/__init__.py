@@ -224,6 +224,18 @@ def ttv_multi(subs: torch.Tensor, vals: torch.Tensor, shape, modes, vecs, *, fmt
     vp = (ctypes.c_void_p * len(vecs))(*[v.data_ptr() for v in vecs])
     lens = (ctypes.c_int64 * len(vecs))(*[v.numel() for v in vecs])
     d = len(shape)
+    if fmt == "auto" and out_subs is None and out_vals is None:
+        # the library allocates the result, so that it can turn it dense
+        o = make_opts(fmt=fmt, path=path, accum=accum, deterministic=deterministic,
+                      workspace=workspace if workspace is not None else None)
+        res = Out()
+        rc = lib.ttv_multi_checked(ctypes.byref(t), m, len(modes), vp, lens, DTYPE[vdt], ctypes.byref(res),
+                                   ctypes.byref(o), _stream_handle(stream))
+        if rc != 0:
+            msg = lib.ttv_last_error().decode(errors="replace")
+            lib.ttv_out_free(ctypes.byref(res))
+            raise TTVError(rc, msg)
+        return _take_result(lib, res)
     rows, nvals = ctypes.c_int64(), ctypes.c_int64()
     if workspace is None:
         o0 = make_opts(fmt=fmt, path=path, accum=accum, deterministic=deterministic)
@@ -515,6 +527,84 @@ def mttkrp(subs, vals, shape, mode: int, factors, stream=None) -> torch.Tensor:
     t = make_tensor(subs, vals, shape)
     _check(lib, lib.ttv_mttkrp(ctypes.byref(t), int(mode), fp, rank, out.data_ptr(), _stream_handle(stream)))
     return out
+
+
+# ---- dense dot product (Eq. 1) and matrix-vector product (Eq. 2) -----------------
+
+def _declare_dense(lib):
+    if getattr(lib, "_dense_declared", False):
+        return lib
+    P = ctypes.POINTER
+    lib.ttv_dot.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    lib.ttv_dot.restype = ctypes.c_int
+    lib.ttv_dot_workspace_size.argtypes = [ctypes.c_int64, P(ctypes.c_size_t)]
+    lib.ttv_dot_workspace_size.restype = ctypes.c_int
+    lib.ttv_matvec.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                               ctypes.c_void_p]
+    lib.ttv_matvec.restype = ctypes.c_int
+    lib.ttv_matvec_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                              P(ctypes.c_size_t)]
+    lib.ttv_matvec_workspace_size.restype = ctypes.c_int
+    lib._dense_declared = True
+    return lib
+
+
+def _dense_operand(t: torch.Tensor, what: str):
+    if not t.is_cuda or t.dtype not in DTYPE:
+        raise ValueError(f"{what} must be a float64 or float32 CUDA tensor")
+
+
+def dot(x: torch.Tensor, y: torch.Tensor, *, out: torch.Tensor | None = None, workspace=None,
+        stream=None) -> torch.Tensor:
+    """x . y (ttv_dot, paper Eq. 1) of two contiguous CUDA vectors of one
+    dtype; returns a one-element float64 CUDA tensor (asynchronous)."""
+    lib = _declare_dense(load())
+    _dense_operand(x, "x")
+    _dense_operand(y, "y")
+    if x.dtype != y.dtype or x.numel() != y.numel() or not x.is_contiguous() or not y.is_contiguous():
+        raise ValueError("x and y must be contiguous, of one dtype and length")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=x.device)
+    nb = workspace.numel() if workspace is not None else 0
+    _check(lib, lib.ttv_dot(x.data_ptr(), y.data_ptr(), x.numel(), DTYPE[x.dtype], out.data_ptr(),
+                            workspace.data_ptr() if workspace is not None else None, nb, _stream_handle(stream)))
+    return out
+
+
+def matvec(A: torch.Tensor, x: torch.Tensor, *, out: torch.Tensor | None = None, workspace=None,
+           stream=None) -> torch.Tensor:
+    """A x (ttv_matvec, paper Eq. 2) for a CUDA matrix in row-major or
+    column-major storage (any strides with one of them 1) and a contiguous
+    vector of the same dtype; returns float64 (asynchronous)."""
+    lib = _declare_dense(load())
+    _dense_operand(A, "A")
+    _dense_operand(x, "x")
+    if A.dim() != 2 or x.dim() != 1 or x.numel() != A.shape[1] or A.dtype != x.dtype or not x.is_contiguous():
+        raise ValueError("A must be (n1, n2) and x a contiguous (n2,) vector of the same dtype")
+    n1, n2 = A.shape
+    if out is None:
+        out = torch.empty(n1, dtype=torch.float64, device=A.device)
+    nb = workspace.numel() if workspace is not None else 0
+    _check(lib, lib.ttv_matvec(A.data_ptr(), n1, n2, A.stride(0), A.stride(1), DTYPE[A.dtype], x.data_ptr(),
+                               out.data_ptr(), workspace.data_ptr() if workspace is not None else None, nb,
+                               _stream_handle(stream)))
+    return out
+
+
+def matvec_workspace_size(A: torch.Tensor) -> int:
+    lib = _declare_dense(load())
+    nb = ctypes.c_size_t()
+    _check(lib, lib.ttv_matvec_workspace_size(A.shape[0], A.shape[1], A.stride(0), A.stride(1), ctypes.byref(nb)))
+    return nb.value
+
+
+def dot_workspace_size(n: int) -> int:
+    lib = _declare_dense(load())
+    nb = ctypes.c_size_t()
+    _check(lib, lib.ttv_dot_workspace_size(int(n), ctypes.byref(nb)))
+    return nb.value
 
 
 # ---- autotuner ------------------------------------------------------------------

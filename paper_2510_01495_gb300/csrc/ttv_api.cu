@@ -36,6 +36,14 @@ void launch_prep_keys(const StreamDesc& p, uint64_t* keys, double* idx, cudaStre
 void launch_prep_gather(const StreamDesc& p, const double* idx_sorted, void* vals_out, const PrepTerms& subs,
                         cudaStream_t stream);
 void launch_prep_count(const uint64_t* keys, int64_t n, unsigned long long* count, cudaStream_t stream);
+void launch_coo_to_dense(const int64_t* subs, const double* vals, int64_t n, int order, const int64_t* shape,
+                         double* dense, int64_t ncells, cudaStream_t stream);
+size_t dot_workspace_bytes(int64_t n);
+void launch_dot(const void* x, const void* y, int64_t n, bool f32, double* out, void* ws, cudaStream_t stream);
+bool matvec_layout_ok(int64_t n1, int64_t n2, int64_t sr, int64_t sc);
+size_t matvec_workspace_bytes(int64_t n1, int64_t n2, int64_t sr, int64_t sc);
+void launch_matvec(const void* A, int64_t n1, int64_t n2, int64_t sr, int64_t sc, bool f32, const void* x,
+                   double* y, void* ws, cudaStream_t stream);
 int64_t mttkrp_nchunks(int64_t n);
 size_t mttkrp_workspace_bytes(int64_t n, int32_t R);
 void launch_mttkrp_chunk_counts(const uint32_t* bits, int64_t n, uint32_t* counts, cudaStream_t stream);
@@ -124,6 +132,8 @@ struct OutState {
     int nonfinite = 0;          // fixed-point path met inf/nan: rerun in binary64
     int retry_sort = 0;         // bucket path gave up: rerun on the sort path
     int borrowed_status = 0;    // status slot belongs to a cached batch graph
+    int auto_fmt = 0;           // TTV_OUT_AUTO: densify at finalisation when more than half full
+    uint64_t nkeys = 0;         // prod(shape[R])
     int rc = TTV_OK;
 };
 
@@ -429,6 +439,47 @@ static size_t workspace_bytes(const Plan& pl) {
     return a.off;
 }
 
+// pyttb's conversion (Sec. 3.3): a sparse result with more than half of its
+// cells present becomes a dense array.  Library-owned results move to a new
+// dense buffer; a caller's value buffer is reused when it holds every cell,
+// else the result stays sparse.
+static int auto_to_dense(ttv_out* out, OutState* s) {
+    const int64_t n = out->nnz, nk = (int64_t)s->nkeys;
+    cudaStream_t stream = s->stream;
+    cudaError_t e = cudaSuccess;
+    if (s->owned_vals) {
+        double* dense = nullptr;
+        e = cudaMallocAsync((void**)&dense, (size_t)nk * sizeof(double), stream);
+        if (e != cudaSuccess) return cuda_fail(e, "dense result allocation");
+        launch_coo_to_dense(out->subs, static_cast<const double*>(out->vals), n, out->order, out->shape, dense,
+                            nk, stream);
+        cudaFreeAsync(s->owned_vals, stream);
+        out->vals = dense;
+        s->owned_vals = dense;
+        out->vals_capacity = nk;
+    } else if (out->vals_capacity >= nk) {
+        double* tmp = nullptr;
+        e = cudaMallocAsync((void**)&tmp, (size_t)std::max<int64_t>(n, 1) * sizeof(double), stream);
+        if (e != cudaSuccess) return cuda_fail(e, "dense conversion scratch");
+        cudaMemcpyAsync(tmp, out->vals, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, stream);
+        launch_coo_to_dense(out->subs, tmp, n, out->order, out->shape, static_cast<double*>(out->vals), nk, stream);
+        cudaFreeAsync(tmp, stream);
+    } else {
+        return TTV_OK;
+    }
+    if (s->owned_subs) {
+        cudaFreeAsync(s->owned_subs, stream);
+        s->owned_subs = nullptr;
+        out->subs = nullptr;
+    }
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "dense conversion");
+    out->is_dense = 1;
+    out->nnz = nk;
+    s->dense_out = 1;
+    return TTV_OK;
+}
+
 static int finalize(ttv_out* out) {
     OutState* s = static_cast<OutState*>(out->internal);
     if (!s) return fail(TTV_ERR_ARG, "result has no pending call");
@@ -450,6 +501,7 @@ static int finalize(ttv_out* out) {
         s->nonfinite = 1;
         return s->rc = fail(TTV_ERR_UNSUPPORTED, "non-finite input on the fixed-point dense path");
     }
+    if (s->auto_fmt && (double)out->nnz > 0.5 * (double)s->nkeys) return s->rc = auto_to_dense(out, s);
     return s->rc = TTV_OK;
 }
 
@@ -460,6 +512,8 @@ static int execute(const Plan& pl, ttv_out* out, const ttv_opts* o, cudaStream_t
     OutState* st = new OutState();
     st->stream = stream;
     st->dense_out = pl.dense_out;
+    st->auto_fmt = o->fmt == TTV_OUT_AUTO && !pl.dense_out && !pl.order0;
+    st->nkeys = p0.nkeys;
     out->internal = st;
     out->order = p0.nr;
     for (int j = 0; j < TTV_MAX_D; ++j) out->shape[j] = j < p0.nr ? p0.rshape[j] : 0;
@@ -1230,6 +1284,69 @@ int ttv_mttkrp(const ttv_tensor* t, int32_t mode, const double* const* factors, 
     }
     ttv_prepared_free(h);
     return rc;
+}
+
+int ttv_dot_workspace_size(int64_t n, size_t* bytes) {
+    if (!bytes || n < 0) return fail(TTV_ERR_ARG, "bad dot arguments");
+    init_once();
+    *bytes = n > 0 ? dot_workspace_bytes(n) : 0;
+    return TTV_OK;
+}
+
+int ttv_dot(const void* x, const void* y, int64_t n, ttv_dtype dtype, double* out, void* workspace,
+            size_t workspace_bytes, ttv_stream_t stream_) {
+    g_err.clear();
+    if (n < 0 || !out || (n > 0 && (!x || !y))) return fail(TTV_ERR_ARG, "null operand or negative length");
+    if (dtype != TTV_F64 && dtype != TTV_F32) return fail(TTV_ERR_ARG, "bad dtype");
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    init_once();
+    const size_t need = n > 0 ? dot_workspace_bytes(n) : 0;
+    void* ws = workspace;
+    bool own = false;
+    if (need && (!ws || workspace_bytes < need)) {
+        cudaError_t e = cudaMallocAsync(&ws, need, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "dot workspace");
+        own = true;
+    }
+    launch_dot(x, y, n, dtype == TTV_F32, out, ws, stream);
+    if (own) cudaFreeAsync(ws, stream);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "dot launch");
+    return TTV_OK;
+}
+
+int ttv_matvec_workspace_size(int64_t n1, int64_t n2, int64_t stride_row, int64_t stride_col, size_t* bytes) {
+    if (!bytes || n1 < 0 || n2 < 0) return fail(TTV_ERR_ARG, "bad matvec arguments");
+    if (!matvec_layout_ok(n1, n2, stride_row, stride_col)) return fail(TTV_ERR_UNSUPPORTED, "neither stride is 1");
+    init_once();
+    *bytes = matvec_workspace_bytes(n1, n2, stride_row, stride_col);
+    return TTV_OK;
+}
+
+int ttv_matvec(const void* A, int64_t n1, int64_t n2, int64_t stride_row, int64_t stride_col, ttv_dtype dtype,
+               const void* x, double* y, void* workspace, size_t workspace_bytes, ttv_stream_t stream_) {
+    g_err.clear();
+    if (n1 < 0 || n2 < 0) return fail(TTV_ERR_ARG, "negative size");
+    if ((n1 > 0 && !y) || (n1 > 0 && n2 > 0 && (!A || !x))) return fail(TTV_ERR_ARG, "null operand");
+    if (dtype != TTV_F64 && dtype != TTV_F32) return fail(TTV_ERR_ARG, "bad dtype");
+    if (!matvec_layout_ok(n1, n2, stride_row, stride_col))
+        return fail(TTV_ERR_UNSUPPORTED, "matrix strides (%lld, %lld): neither is 1", (long long)stride_row,
+                    (long long)stride_col);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    init_once();
+    const size_t need = matvec_workspace_bytes(n1, n2, stride_row, stride_col);
+    void* ws = workspace;
+    bool own = false;
+    if (need && (!ws || workspace_bytes < need)) {
+        cudaError_t e = cudaMallocAsync(&ws, need, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "matvec workspace");
+        own = true;
+    }
+    launch_matvec(A, n1, n2, stride_row, stride_col, dtype == TTV_F32, x, y, ws, stream);
+    if (own) cudaFreeAsync(ws, stream);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "matvec launch");
+    return TTV_OK;
 }
 
 int ttv_prepared_info(const ttv_prepared* h, int64_t* nnz_out, int32_t* order, size_t* device_bytes) {

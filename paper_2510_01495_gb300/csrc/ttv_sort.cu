@@ -717,6 +717,9 @@ struct RbkScanSmem {
     uint32_t cnt[kRbkThreads / 32];
     uint32_t flag[kRbkThreads / 32];
     double val[kRbkThreads / 32];
+    uint32_t pcnt[kRbkThreads / 32 + 1];   // exclusive prefix of warp w; [8]: the tile total
+    uint32_t pflag[kRbkThreads / 32 + 1];
+    double pval[kRbkThreads / 32 + 1];
 };
 
 __device__ __forceinline__ void rbk_block_scan(const RbkPairs& r, RbkScanSmem& ss, uint32_t& xc, uint32_t& xf,
@@ -741,24 +744,31 @@ __device__ __forceinline__ void rbk_block_scan(const RbkPairs& r, RbkScanSmem& s
     xv = __shfl_up_sync(0xffffffffu, v, 1);
     if (lane == 0) { xc = 0; xf = 0; xv = 0.0; }
     __syncthreads();
-    // warp prefix, left to right over the 8 warps (every thread computes it)
-    uint32_t pc = 0, pf = 0;
-    double pv = 0.0;
+    // warp prefixes, folded left to right over the 8 warps by one thread
+    if (threadIdx.x == 0) {
+        uint32_t pc = ss.cnt[0], pf = ss.flag[0];
+        double pv = ss.val[0];
 #pragma unroll
-    for (int w = 0; w < kRbkThreads / 32; ++w) {
-        if (w == warp) {
-            if (w > 0) seg_combine(pc, pf, pv, xc, xf, xv);
+        for (int w = 1; w < kRbkThreads / 32; ++w) {
+            ss.pcnt[w] = pc;
+            ss.pflag[w] = pf;
+            ss.pval[w] = pv;
+            uint32_t cw = ss.cnt[w], fw = ss.flag[w];
+            double vw = ss.val[w];
+            seg_combine(pc, pf, pv, cw, fw, vw);
+            pc = cw;
+            pf = fw;
+            pv = vw;
         }
-        uint32_t cw = ss.cnt[w], fw = ss.flag[w];
-        double vw = ss.val[w];
-        if (w > 0) seg_combine(pc, pf, pv, cw, fw, vw);
-        pc = cw;
-        pf = fw;
-        pv = vw;
+        ss.pcnt[kRbkThreads / 32] = pc;
+        ss.pflag[kRbkThreads / 32] = pf;
+        ss.pval[kRbkThreads / 32] = pv;
     }
-    tc = pc;
-    tf = pf;
-    tv = pv;
+    __syncthreads();
+    if (warp > 0) seg_combine(ss.pcnt[warp], ss.pflag[warp], ss.pval[warp], xc, xf, xv);
+    tc = ss.pcnt[kRbkThreads / 32];
+    tf = ss.pflag[kRbkThreads / 32];
+    tv = ss.pval[kRbkThreads / 32];
 }
 
 // A tile's summary needs its head count and the sum of the terms after its

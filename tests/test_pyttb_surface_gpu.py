@@ -67,3 +67,33 @@ def test_all_modes_returns_a_float(cuda_lib):
     assert isinstance(x, float)
     ref, A = oracle_ttv(t.subs, t.vals, t.shape, [0, 1, 2], vecs)
     assert_close([x], ref[1], A, what="order 0")
+
+
+def test_auto_format_with_caller_buffers(cuda_lib):
+    """The automatic format on caller-provided buffers: converted in place
+    when the value buffer holds every cell, left sparse otherwise."""
+    t, vecs = tensor(8, (20, 30, 40), 20_000)
+    subs, vals = t.subs.cuda(), t.vals.cuda()
+    v = vecs[2].cuda()
+    big = torch.empty(600, dtype=torch.float64, device="cuda")
+    rows = torch.empty((600, 2), dtype=torch.int64, device="cuda")
+    r = ttv.ttv_multi(subs, vals, t.shape, [2], [v], fmt="auto", out_vals=big, out_subs=rows)
+    ref, A = oracle_ttv(t.subs, t.vals, t.shape, [2], [vecs[2]], dense=True)
+    assert r.is_dense
+    check_result(r, ref, A, dense=True, what="auto, caller buffers")
+    # 600 nonzeros fill about 63 % of the 600 cells: dense by the rule, but a
+    # value buffer of exactly the sparse size keeps it sparse
+    t2, v2 = tensor(9, (20, 30, 40), 600)
+    ref2, A2 = oracle_ttv(t2.subs, t2.vals, t2.shape, [2], [v2[2]])
+    n_out = ref2[1].size
+    assert 300 < n_out < 600
+    small = torch.empty(n_out, dtype=torch.float64, device="cuda")
+    small_rows = torch.empty((n_out, 2), dtype=torch.int64, device="cuda")
+    r2 = ttv.ttv_multi(t2.subs.cuda(), t2.vals.cuda(), t2.shape, [2], [v2[2].cuda()], fmt="auto", out_vals=small,
+                       out_subs=small_rows)
+    assert not r2.is_dense
+    check_result(r2, ref2, A2, what="auto, small caller buffers")
+    r3 = ttv.ttv(t2.subs.cuda(), t2.vals.cuda(), t2.shape, v2[2].cuda(), dims=2)     # library buffers
+    assert r3.is_dense
+    ref3, A3 = oracle_ttv(t2.subs, t2.vals, t2.shape, [2], [v2[2]], dense=True)
+    check_result(r3, ref3, A3, dense=True, what="auto, library buffers")
