@@ -507,6 +507,7 @@ struct RbkPairs {
     int64_t g0;
     uint32_t heads, cnt, flag;
     double open;
+    double first_done;           // done[] at this thread's first head (0 when it has none)
 };
 
 // Terms of the sort path: stored next to the sorted keys.
@@ -657,12 +658,15 @@ __device__ __forceinline__ void rbk_load(const H& hd, const Src& src, int64_t n,
         r.cnt = __popc(r.heads);
         r.flag = r.heads != 0;
         double acc = 0.0;
+        r.first_done = 0.0;
+        const int fh = r.heads ? __ffs(r.heads) - 1 : kRbkItems;
 #pragma unroll
         for (int i = 0; i < kRbkItems; ++i) {
             r.done[i] = 0.0;
             if (i < r.nmine) {
                 if ((r.heads >> i) & 1u) {
                     r.done[i] = acc;
+                    if (i == fh) r.first_done = acc;
                     acc = r.v[i];
                 } else {
                     acc = acc + r.v[i];
@@ -692,11 +696,13 @@ __device__ __forceinline__ void rbk_load(const H& hd, const Src& src, int64_t n,
     r.flag = 0;
     double acc = 0.0;
     uint64_t prev = r.prev0;
+    r.first_done = 0.0;
 #pragma unroll
     for (int i = 0; i < kRbkItems; ++i) {
         r.done[i] = 0.0;
         if (i < r.nmine) {
             if (r.k[i] != prev || r.g0 + i == 0) {
+                if (!r.flag) r.first_done = acc;
                 r.heads |= 1u << i;
                 ++r.cnt;
                 r.flag = 1;
@@ -952,17 +958,19 @@ __global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(H hd, Src src, int6
     const int first = tile == 0 ? 1 : 0;
     int h = (int)xc;
     uint64_t prev = r.prev0;
-    bool seen = false;
+    // the first head closes the run open at the range start: its sum is
+    // base + the part formed here (one add per thread, not per head)
+    const int fh = r.heads ? __ffs(r.heads) - 1 : kRbkItems;
+    const double closed_first = base + r.first_done;
 #pragma unroll
     for (int i = 0; i < kRbkItems; ++i) {
         if (i < r.nmine) {
             if ((r.heads >> i) & 1u) {
                 if (r.g0 + i > 0) {
                     if constexpr (!H::kBits) sm.row_key[h - first] = prev;
-                    sm.row_val[h - first] = seen ? r.done[i] : base + r.done[i];
+                    sm.row_val[h - first] = i == fh ? closed_first : r.done[i];
                 }
                 ++h;
-                seen = true;
             }
             prev = r.k[i];
         }
