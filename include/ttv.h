@@ -222,7 +222,9 @@ void ttv_batch_release(void);
  * candidate on the given problem -- accumulation path (DENSE, SORT, HASH,
  * BUCKET) x CTAs per SM of the streaming pass (2/3/4 for DENSE, 4/8/16 for
  * SORT, 8/16 for HASH) x nonzeros per thread per iteration (DENSE: 1 or 2
- * pairs; HASH: 2 or 4) -- `trials` times after one warm-up run each, takes
+ * pairs, or 4 = the bulk-staged persistent kernel with one CTA per SM;
+ * HASH: 2 or 4) -- `trials` times
+ * after one warm-up run each, takes
  * the median of CUDA-event times on `stream`, and records the fastest for
  * the class.
  * Every later call with path AUTO, fp64 accumulation and no determinism
@@ -257,6 +259,13 @@ int ttv_tune_load(const char *path);     /* TTV_ERR_ARG on a missing or malforme
                                             nothing is merged then                     */
 void ttv_tune_clear(void);
 int ttv_tune_count(void);                /* recorded classes */
+/* Records a plan for the problem's class by hand, as ttv_autotune would:
+ * a concrete path (DENSE, SORT, HASH, BUCKET), CTAs per SM (0: default) and
+ * items per thread (0: default), with the meanings listed above.  A path
+ * that does not apply to a later problem of the class falls back as for an
+ * autotuned record.  TTV_ERR_ARG for an invalid problem or plan. */
+int ttv_tune_set(const ttv_tensor *t, const int32_t *modes, int32_t n_v, const ttv_opts *opts, int32_t path,
+                 int32_t ctas_per_sm, int32_t items_per_thread);
 /* 1 and the recorded plan if the problem's class (vectors taken as FP64 for
  * the class key) has a record, 0 if not, a negative error code for an
  * invalid problem.  path / ctas_per_sm / items_per_thread may be NULL. */

@@ -638,6 +638,9 @@ def _declare_tune(lib):
     lib.ttv_tune_lookup.argtypes = [P(Tensor), P(ctypes.c_int32), ctypes.c_int32, P(Opts), P(ctypes.c_int32),
                                     P(ctypes.c_int32), P(ctypes.c_int32)]
     lib.ttv_tune_lookup.restype = ctypes.c_int
+    lib.ttv_tune_set.argtypes = [P(Tensor), P(ctypes.c_int32), ctypes.c_int32, P(Opts), ctypes.c_int32,
+                                 ctypes.c_int32, ctypes.c_int32]
+    lib.ttv_tune_set.restype = ctypes.c_int
     lib._tune_declared = True
     return lib
 
@@ -673,6 +676,17 @@ def tune_lookup(subs, vals, shape, modes, *, fmt="sparse"):
     if rc < 0:
         _check(lib, rc)
     return (PATH_NAME[pth.value], ctas.value, items.value) if rc == 1 else None
+
+
+def tune_set(subs, vals, shape, modes, path: str, ctas_per_sm: int = 0, items_per_thread: int = 0, *,
+             fmt="sparse"):
+    """Records a plan for this problem's class by hand (ttv_tune_set)."""
+    lib = _declare_tune(load())
+    t = make_tensor(subs, vals, shape)
+    m = (ctypes.c_int32 * len(modes))(*[int(x) for x in modes])
+    o = make_opts(fmt=fmt)
+    _check(lib, lib.ttv_tune_set(ctypes.byref(t), m, len(modes), ctypes.byref(o), PATH[path], int(ctas_per_sm),
+                                 int(items_per_thread)))
 
 
 def tune_save(path: str):

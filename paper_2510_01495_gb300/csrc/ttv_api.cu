@@ -887,13 +887,16 @@ int ttv_autotune(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const v
     const uint64_t key = tune_key(p, base.dense_out);
 
     // candidates: path x CTAs per SM of the streaming pass x nonzeros per
-    // thread (DENSE: 1 or 2 pairs per iteration; HASH: 2 or 4 per iteration)
+    // thread (DENSE: 1 or 2 pairs per iteration, or 4 = the bulk-staged
+    // persistent kernel, one CTA per SM; HASH: 2 or 4 per iteration)
     struct Cand { int path, ctas, items; };
     std::vector<Cand> cands;
     const bool dense_ok = (int64_t)p.nkeys <= kDenseMaxCells || base.order0;
-    if (dense_ok)
+    if (dense_ok) {
+        cands.push_back({TTV_PATH_DENSE, 1, 4});
         for (int it : {1, 2})
             for (int c : {2, 3, 4}) cands.push_back({TTV_PATH_DENSE, c, it});
+    }
     if (!base.order0 && p.nnz > 0 && p.nnz <= kMaxSortN) {
         for (int c : {4, 8, 16}) cands.push_back({TTV_PATH_SORT, c, 0});
         if (hash_applicable(p))
@@ -1017,6 +1020,30 @@ int ttv_tune_lookup(const ttv_tensor* t, const int32_t* modes, int32_t n_v, cons
     if (ctas_per_sm) *ctas_per_sm = r.ctas;
     if (items_per_thread) *items_per_thread = r.items;
     return 1;
+}
+
+int ttv_tune_set(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const ttv_opts* opts, int32_t path,
+                 int32_t ctas_per_sm, int32_t items_per_thread) {
+    g_err.clear();
+    if (path < TTV_PATH_DENSE || path > TTV_PATH_BUCKET) return fail(TTV_ERR_ARG, "path %d is not a concrete path", path);
+    if (ctas_per_sm < 0 || ctas_per_sm > 32 || items_per_thread < 0 || items_per_thread > 8)
+        return fail(TTV_ERR_ARG, "CTAs per SM or items per thread out of range");
+    ttv_opts o;
+    if (opts) o = *opts;
+    else ttv_opts_init(&o);
+    o.path = TTV_PATH_AUTO;
+    std::vector<const void*> dummy((size_t)std::max(n_v, 0), reinterpret_cast<const void*>(0x10));
+    Plan pl;
+    t_force_path = -1;
+    const int rc = make_plan(t, modes, n_v, dummy.data(), TTV_F64, nullptr, &o, pl);
+    if (rc != TTV_OK) return rc;
+    TuneRec r;
+    r.path = path;
+    r.ctas = ctas_per_sm;
+    r.items = items_per_thread;
+    r.ms = 0.0;
+    tune_record(tune_key(pl.desc, pl.dense_out), r);
+    return TTV_OK;
 }
 
 void ttv_tune_clear(void) {

@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "ttv_internal.cuh"
+#include "ttv_tma.cuh"
 
 namespace ttv {
 
@@ -150,6 +151,189 @@ __global__ void __launch_bounds__(kVecThreads, kVecPairs == 1 ? 4 : 3) k_dense_v
     }
 }
 
+// ---- bulk-staged persistent variant -------------------------------------------
+// One CTA per SM.  A producer warp streams the CTA's range of nonzeros into
+// shared memory, tile by tile, with cp.async.bulk copies that complete on a
+// per-stage mbarrier; 31 consumer warps form the terms from the staged
+// subscripts and values and add them into the shared accumulator, then
+// release the stage on a second mbarrier.  The loads stay in flight (up to
+// four tiles) while the consumers work, instead of every thread waiting on
+// its own global loads.
+constexpr int kTmaThreads = 1024;
+constexpr int kTmaConsumers = kTmaThreads - 32;     // warps 0..30
+constexpr int kTmaTile = 2 * kTmaConsumers;          // 1984 nonzeros per stage
+constexpr int kTmaMaxStages = 4;
+constexpr size_t kTmaSmemMax = 226 * 1024;   // under the 227 KB opt-in, with room for static shared memory
+
+struct TmaLayout {
+    size_t pres_off, vec_off, stage_off, bar_off, total, stage_bytes;
+    int stages;
+};
+
+static TmaLayout tma_layout(const StreamDesc& p, int want_presence, bool intp) {
+    TmaLayout L{};
+    size_t off = (size_t)p.nkeys * sizeof(double);
+    L.pres_off = off;
+    if (want_presence) off += ((p.nkeys + 31) / 32) * sizeof(uint32_t);
+    off = (off + 15) & ~size_t(15);
+    L.vec_off = off;
+    off += (size_t)p.vtotal * (intp ? sizeof(SigEntry) : sizeof(double));
+    off = (off + 127) & ~size_t(127);
+    L.stage_off = off;
+    const size_t vb = p.val_f32 ? 4 : 8;
+    L.stage_bytes = (size_t)kTmaTile * (8 * (size_t)p.d + vb);
+    L.stage_bytes = (L.stage_bytes + 127) & ~size_t(127);
+    const size_t bars = 2 * kTmaMaxStages * sizeof(uint64_t);
+    const size_t room = kTmaSmemMax > off + bars ? kTmaSmemMax - off - bars : 0;
+    L.stages = (int)std::min<size_t>(kTmaMaxStages, room / L.stage_bytes);
+    L.bar_off = off + (size_t)std::max(L.stages, 0) * L.stage_bytes;
+    L.total = L.bar_off + bars;
+    return L;
+}
+
+template <int D, bool kSoA, bool kIntP>
+__global__ void __launch_bounds__(kTmaThreads, 1) k_dense_tma(StreamDesc p, int64_t chunk, int want_presence,
+                                                             TmaLayout L, double* __restrict__ partials,
+                                                             uint32_t* __restrict__ pres_partials) {
+    extern __shared__ __align__(128) unsigned char tsm[];
+    double* acc = reinterpret_cast<double*>(tsm);
+    uint32_t* pres = reinterpret_cast<uint32_t*>(tsm + L.pres_off);
+    double* sv = reinterpret_cast<double*>(tsm + L.vec_off);
+    SigEntry* sve = reinterpret_cast<SigEntry*>(tsm + L.vec_off);
+    unsigned char* stage0 = tsm + L.stage_off;
+    uint64_t* full = reinterpret_cast<uint64_t*>(tsm + L.bar_off);
+    uint64_t* empty = full + kTmaMaxStages;
+    __shared__ int s_err;
+    __shared__ long long s_issued;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int S = L.stages;
+    const int64_t P = (int64_t)p.nkeys;
+    const int64_t npres = (P + 31) / 32;
+    for (int64_t i = tid; i < P; i += kTmaThreads) acc[i] = 0.0;
+    if (want_presence)
+        for (int64_t i = tid; i < npres; i += kTmaThreads) pres[i] = 0u;
+    if (kIntP) stage_vectors_sig(p, sve);
+    else stage_vectors(p, sv);
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kTmaConsumers / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_err = 0;
+        s_issued = 0;
+    }
+    __syncthreads();
+
+    const int64_t lo = (int64_t)blockIdx.x * chunk;     // a multiple of 4
+    const int64_t hi = min(p.nnz, lo + chunk);
+    const int64_t ntiles = hi > lo ? (hi - lo + kTmaTile - 1) / kTmaTile : 0;
+    const int vb = p.val_f32 ? 4 : 8;
+    const double* vd = static_cast<const double*>(p.vals);
+    const float* vf = static_cast<const float*>(p.vals);
+
+    if (warp == kTmaThreads / 32 - 1) {
+        // producer: tile i goes to stage i % S once its previous use is released
+        if (lane == 0) {
+            int64_t i = 0;
+            for (; i < ntiles; ++i) {
+                const int s = (int)(i % S);
+                if (i >= S && !mbar_wait(&empty[s], (uint32_t)(((i / S) - 1) & 1))) {
+                    set_error(p.status, kErrTimeout);
+                    s_err = 1;
+                    break;
+                }
+                const int64_t k0 = lo + i * kTmaTile;
+                const int cnt = (int)min((int64_t)kTmaTile, hi - k0);
+                unsigned char* st = stage0 + (size_t)s * L.stage_bytes;
+                // copies of whole 16-byte units; the few elements past them are read directly
+                const uint32_t sb = kSoA ? (uint32_t)(cnt & ~1) * 8u : ((uint32_t)cnt * 8u * D) & ~15u;
+                const uint32_t vbytes = p.val_f32 ? (uint32_t)(cnt & ~3) * 4u : (uint32_t)(cnt & ~1) * 8u;
+                mbar_expect_tx(&full[s], (kSoA ? sb * D : sb) + vbytes);
+                if (kSoA) {
+                    if (sb)
+#pragma unroll
+                        for (int m = 0; m < D; ++m)
+                            bulk_g2s(st + (size_t)m * kTmaTile * 8, p.subs + (int64_t)m * p.smode + k0, sb, &full[s]);
+                } else if (sb) {
+                    bulk_g2s(st, p.subs + k0 * D, sb, &full[s]);
+                }
+                if (vbytes)
+                    bulk_g2s(st + (size_t)D * kTmaTile * 8, static_cast<const unsigned char*>(p.vals) + k0 * vb,
+                             vbytes, &full[s]);
+            }
+            s_issued = i;
+        }
+    } else {
+        // consumers: two nonzeros of every tile per thread
+        for (int64_t i = 0; i < ntiles; ++i) {
+            const int s = (int)(i % S);
+            if (!mbar_wait(&full[s], (uint32_t)((i / S) & 1))) {
+                set_error(p.status, kErrTimeout);
+                s_err = 1;
+                break;
+            }
+            const int64_t k0 = lo + i * kTmaTile;
+            const int cnt = (int)min((int64_t)kTmaTile, hi - k0);
+            const unsigned char* st = stage0 + (size_t)s * L.stage_bytes;
+            const int64_t* scol = reinterpret_cast<const int64_t*>(st);
+            const int cs = kSoA ? (cnt & ~1) : (int)((((uint32_t)cnt * 8u * D) & ~15u) / 8u);
+            const int cv = p.val_f32 ? (cnt & ~3) : (cnt & ~1);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int j = tid + u * kTmaConsumers;
+                if (j >= cnt) continue;
+                const int64_t k = k0 + j;
+                int64_t sj[D];
+#pragma unroll
+                for (int m = 0; m < D; ++m) {
+                    if (kSoA) sj[m] = j < cs ? scol[(size_t)m * kTmaTile + j] : p.subs[(int64_t)m * p.smode + k];
+                    else sj[m] = j * D + m < cs ? scol[j * D + m] : p.subs[k * D + m];
+                }
+                double v;
+                if (j < cv) v = p.val_f32 ? (double)reinterpret_cast<const float*>(st + (size_t)D * kTmaTile * 8)[j]
+                                          : reinterpret_cast<const double*>(st + (size_t)D * kTmaTile * 8)[j];
+                else v = p.val_f32 ? (double)vf[k] : vd[k];
+                dense_item<D, kIntP>(p, sv, sve, sj, v, acc, pres, want_presence);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && s_err) {
+        // a wait ran out: let every copy already issued land before the CTA exits
+        const int64_t issued = s_issued;
+        for (int64_t i = max((int64_t)0, issued - S); i < issued; ++i)
+            mbar_wait(&full[i % S], (uint32_t)((i / S) & 1), 1u << 20);
+    }
+    double* my = partials + (size_t)blockIdx.x * P;
+    for (int64_t i = tid; i < P; i += kTmaThreads) my[i] = acc[i];
+    if (want_presence) {
+        uint32_t* mp = pres_partials + (size_t)blockIdx.x * npres;
+        for (int64_t i = tid; i < npres; i += kTmaThreads) mp[i] = pres[i];
+    }
+}
+
+typedef void (*DenseTmaKernel)(StreamDesc, int64_t, int, TmaLayout, double*, uint32_t*);
+
+template <int D>
+static DenseTmaKernel pick_tma(bool soa, bool intp) {
+    if (soa) return intp ? k_dense_tma<D, true, true> : k_dense_tma<D, true, false>;
+    return intp ? k_dense_tma<D, false, true> : k_dense_tma<D, false, false>;
+}
+
+static DenseTmaKernel dense_tma_kernel(int d, bool soa, bool intp) {
+    switch (d) {
+        case 2: return pick_tma<2>(soa, intp);
+        case 3: return pick_tma<3>(soa, intp);
+        case 4: return pick_tma<4>(soa, intp);
+        case 5: return pick_tma<5>(soa, intp);
+        case 6: return pick_tma<6>(soa, intp);
+        default: return nullptr;
+    }
+}
+
 // ---- host side ------------------------------------------------------------
 typedef void (*DenseVecKernel)(StreamDesc, int64_t, int, size_t, size_t, double*, uint32_t*);
 
@@ -198,7 +382,28 @@ size_t dense_vec_smem(const StreamDesc& p, int want_presence) {
     return off;
 }
 
+int dense_vec_products_int(const StreamDesc& p);
+
+// The bulk-staged kernel is the autotuner's items == 4 candidate, used when
+// at least two stages fit beside the accumulator and the staged vectors and
+// there are enough nonzeros for every SM to stream several tiles.  It is not
+// the default: on the all-but-one 1000^4 problem it takes 113 us against the
+// register-loading kernel's 105 us, because the limit there is the shared
+// memory atomics and significand loads, not the global loads it overlaps.
+static bool use_tma(const StreamDesc& p, int want_presence) {
+    if (p.items != 4) return false;
+    if (p.val_f32 && (reinterpret_cast<uintptr_t>(p.vals) & 15)) return false;
+    if (p.nnz < (int64_t)num_sms() * kTmaTile * 2) return false;
+    return tma_layout(p, want_presence, dense_vec_products_int(p) != 0).stages >= 2;
+}
+
+static int64_t tma_chunk(const StreamDesc& p, int G) {
+    int64_t chunk = (p.nnz + G - 1) / G;
+    return (chunk + 3) & ~int64_t(3);
+}
+
 int dense_vec_grid(const StreamDesc& p, int want_presence) {
+    if (use_tma(p, want_presence)) return num_sms();
     const bool soa = p.snz == 1;
     DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p), dense_vec_pairs(p));
     const size_t smem = dense_vec_smem(p, want_presence);
@@ -215,6 +420,16 @@ int dense_vec_grid(const StreamDesc& p, int want_presence) {
 void launch_dense_vec(const StreamDesc& p, int want_presence, int G, double* partials, uint32_t* pres_partials,
                       cudaStream_t stream) {
     const bool soa = p.snz == 1;
+    if (use_tma(p, want_presence) && G == num_sms()) {
+        const bool intp = dense_vec_products_int(p) != 0;
+        DenseTmaKernel k = dense_tma_kernel(p.d, soa, intp);
+        const TmaLayout L = tma_layout(p, want_presence, intp);
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+        TTV_LAUNCH("dense_accum", stream,
+                   k<<<G, kTmaThreads, L.total, stream>>>(p, tma_chunk(p, G), want_presence, L, partials,
+                                                          pres_partials));
+        return;
+    }
     DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p), dense_vec_pairs(p));
     const size_t smem = dense_vec_smem(p, want_presence);
     size_t pres_off = (size_t)p.nkeys * sizeof(double);

@@ -398,3 +398,47 @@ def test_keys_above_2_63(cuda_lib, path):
     p = S.Problem(S.SparseTensor(torch.from_numpy(subs), torch.from_numpy(vals), shape), [4],
                   [torch.from_numpy(x)], name="top_bit_keys")
     run_case(cuda_lib, p, path=path, layout="soa")
+
+
+@pytest.mark.parametrize("layout", ["soa", "aos"])
+@pytest.mark.parametrize("case", [
+    ((60, 70, 80, 50), 700_001, [0, 1, 3], "dense"),
+    ((60, 70, 80, 50), 1_234_567, [0, 2, 3], "sparse"),      # presence bitmap: sparse result off the dense path
+    ((300, 200, 100), 900_002, [1, 2], "dense"),
+    ((30, 40, 50, 60, 70), 1_000_003, [0, 1, 3, 4], "dense"),
+])
+def test_dense_staged_kernel(cuda_lib, case, layout):
+    """Sizes above the point where the dense path switches to the
+    bulk-staged persistent kernel: ragged last tiles, odd counts (the element
+    past the last 16-byte unit is read directly), both layouts."""
+    shape, nnz, modes, fmt = case
+    p = rand_problem(31 + nnz, shape, nnz, modes)
+    with staged_dense_plan(cuda_lib, p, fmt, layout):
+        run_case(cuda_lib, p, path="auto", fmt=fmt, layout=layout)
+
+
+class staged_dense_plan:
+    """Pins the bulk-staged dense kernel (DENSE, items 4) for the problem's
+    class for the duration of a block, through a hand-set tuning record."""
+
+    def __init__(self, ttv, problem, fmt, layout, val_dtype=torch.float64):
+        self.ttv = ttv
+        subs, vals, _ = to_device(problem, layout=layout, val_dtype=val_dtype)
+        self.args = (subs, vals, problem.tensor.shape, problem.modes)
+        self.fmt = fmt
+
+    def __enter__(self):
+        self.ttv.tune_clear()
+        self.ttv.tune_set(*self.args, "dense", 1, 4, fmt=self.fmt)
+        assert self.ttv.tune_lookup(*self.args, fmt=self.fmt) == ("dense", 1, 4)
+
+    def __exit__(self, *exc):
+        self.ttv.tune_clear()
+
+
+def test_dense_staged_kernel_float32(cuda_lib):
+    p = rand_problem(41, (60, 70, 80, 50), 800_003, [0, 1, 3])
+    with staged_dense_plan(cuda_lib, p, "dense", "soa", torch.float32):
+        run_case(cuda_lib, p, path="auto", fmt="dense", layout="soa", val_dtype=torch.float32)
+    with staged_dense_plan(cuda_lib, p, "dense", "aos", torch.float32):
+        run_case(cuda_lib, p, path="auto", fmt="dense", layout="aos", val_dtype=torch.float32)
