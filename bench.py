@@ -91,9 +91,9 @@ DOMINANT = {"allbutone_4way_1000": [("dense_accum", _stream_bytes), ("dense_fx",
 TRAFFIC = {
     "allbutone_4way_1000": {
         "kernel": "dense_accum",
-        "files": ["ttv_dense_vec.cu", "ttv_internal.cuh", "ttv_udiv.h"],
-        "sha": "d68ab89cdbab",
-        "bytes_per_launch": 400288085,   # 400.08 MB read + 0.21 MB written, mean of 45 launches
+        "files": ["ttv_dense_vec.cu", "ttv_internal.cuh", "ttv_udiv.h", "ttv_tma.cuh"],
+        "sha": "cbcfd784a6c0",
+        "bytes_per_launch": 400297495,   # 400.08 MB read + 0.21 MB written, mean of 45 launches
     },
 }
 
