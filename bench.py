@@ -182,6 +182,31 @@ def algorithmic_bytes(problem, nnz_out: int, w: int = 8) -> dict:
             "gathered_per_nonzero": t.nnz * len(problem.modes) * w}
 
 
+def cpu_parallel_sample(problem, target_s: float = 5.0, max_nnz: int = 20_000_000):
+    """The same definition on all allowed host cores (the oracle's OpenMP
+    statement, bit-identical to it) on the first m nonzeros; GNNZ/s, m,
+    seconds, threads -- or None when it could not be built."""
+    import oracle
+    try:
+        oracle.build_parallel()
+        threads = oracle.parallel_threads()
+    except Exception:   # noqa: BLE001
+        return None
+    t = problem.tensor
+    subs = t.subs.cpu().numpy()
+    vals = t.vals.cpu().numpy()
+    vecs = [v.cpu().numpy() for v in problem.vecs]
+    m = min(t.nnz, 500_000)
+    t0 = time.perf_counter()
+    oracle.ttv_parallel(subs[:m], vals[:m], t.shape, problem.modes, vecs, dense=problem.dense)
+    dt = time.perf_counter() - t0
+    m2 = int(min(t.nnz, max_nnz, max(m, m * target_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.ttv_parallel(subs[:m2], vals[:m2], t.shape, problem.modes, vecs, dense=problem.dense)
+    dt2 = time.perf_counter() - t0
+    return m2 / dt2 / 1e9, m2, dt2, threads
+
+
 def cpu_oracle_sample(problem, target_s: float = 10.0, max_nnz: int = 20_000_000):
     """The CPU oracle on the first m nonzeros of the workload (m chosen so the
     call runs ~target_s seconds, at most max_nnz); returns GNNZ/s and what was run."""
@@ -505,6 +530,13 @@ def main():
         v, m, dt = cpu_oracle_sample(problem)
         line["cpu_baseline"] = {"value": v, "unit": "GNNZ/s", "cores": 1, "kind": "oracle",
                                 "sample": f"first {m} of {nnz} nonzeros, one call, {dt:.1f} s"}
+        par = cpu_parallel_sample(problem)
+        if par is not None:
+            pv, pm, pdt, pth = par
+            line["cpu_baseline_parallel"] = {
+                "value": pv, "unit": "GNNZ/s", "cores": pth, "kind": "oracle-openmp",
+                "sample": f"first {pm} of {nnz} nonzeros, one call, {pdt:.1f} s; per-thread sorts of contiguous "
+                          f"ranges merged into the one-core oracle's order (bit-identical result)"}
     if dist:
         dist.destroy_process_group()
     if rank == 0:

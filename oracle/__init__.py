@@ -250,3 +250,86 @@ def matvec(A, x, lib=None) -> np.ndarray:
     if rc != 0:
         raise OracleError(rc)
     return y
+
+
+# ---- the same TTV definition on all host cores (OpenMP), for the benchmark's
+# multi-core CPU baseline; bit-identical to ``ttv`` (tests/test_oracle_pins.py)
+
+_OMP_SRC = os.path.join(_HERE, "ttv_oracle_omp.c")
+_OMP_LIB_PATH = os.path.join(_BUILD_DIR, "libttv_oracle_omp.so")
+_omp_lib = None
+
+
+def build_parallel() -> str:
+    """Build the OpenMP statement if it is missing or older than its source."""
+    if (not os.path.exists(_OMP_LIB_PATH)
+            or os.path.getmtime(_OMP_LIB_PATH) < os.path.getmtime(_OMP_SRC)):
+        compile_library(_OMP_SRC, _OMP_LIB_PATH, extra_flags=("-fopenmp",))
+    return _OMP_LIB_PATH
+
+
+def _get_omp_lib():
+    global _omp_lib
+    with _lock:
+        if _omp_lib is None:
+            lib = ctypes.CDLL(build_parallel())
+            lib.oracle_ttv_omp.restype = ctypes.c_int
+            lib.oracle_ttv_omp.argtypes = [
+                ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), ctypes.c_int32, ctypes.c_int32,
+                ctypes.POINTER(_Out)]
+            lib.oracle_omp_free.restype = None
+            lib.oracle_omp_free.argtypes = [ctypes.POINTER(_Out)]
+            lib.oracle_omp_max_threads.restype = ctypes.c_int
+            _omp_lib = lib
+    return _omp_lib
+
+
+def parallel_threads() -> int:
+    """Threads the OpenMP statement uses by default (all allowed cores)."""
+    return int(_get_omp_lib().oracle_omp_max_threads())
+
+
+def ttv_parallel(subs, vals, shape, modes, vecs, dense: bool = False, threads: int = 0):
+    """``ttv`` on ``threads`` host cores (0: all); same result, bit for bit."""
+    lib = _get_omp_lib()
+    if np.isscalar(modes):
+        modes, vecs = [int(modes)], [vecs]
+    shape = np.ascontiguousarray(np.asarray(shape, dtype=np.int64).reshape(-1))
+    d = int(shape.size)
+    subs = np.ascontiguousarray(np.asarray(subs, dtype=np.int64).reshape(-1, d))
+    vals = _as_f64(vals).reshape(-1)
+    if subs.shape[0] != vals.shape[0]:
+        raise ValueError("subs and vals disagree on nnz")
+    modes_a = np.ascontiguousarray(np.asarray(modes, dtype=np.int32).reshape(-1))
+    vec_arrs = [_as_f64(v).reshape(-1) for v in vecs]
+    if len(vec_arrs) != modes_a.size:
+        raise ValueError("one vector per contracted mode")
+    lens = np.ascontiguousarray(np.array([v.size for v in vec_arrs], dtype=np.int64))
+    ptr_arr = (ctypes.POINTER(ctypes.c_double) * max(1, len(vec_arrs)))(
+        *[v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for v in vec_arrs])
+    out = _Out()
+    rc = lib.oracle_ttv_omp(
+        d, shape.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(vals.size),
+        subs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        int(modes_a.size), modes_a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+        lens.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ptr_arr, 1 if dense else 0, int(threads),
+        ctypes.byref(out))
+    if rc != 0:
+        raise OracleError(rc)
+    try:
+        order = out.order
+        newshape = tuple(int(out.shape[j]) for j in range(order))
+        n = int(out.nnz)
+        vals_out = np.ctypeslib.as_array(out.vals, shape=(max(n, 1),))[:n].copy()
+        if dense:
+            return None, vals_out.reshape(newshape), newshape
+        if order > 0 and n > 0:
+            subs_out = np.ctypeslib.as_array(out.subs, shape=(n * order,)).copy().reshape(n, order)
+        else:
+            subs_out = np.zeros((n, order), dtype=np.int64)
+        return subs_out, vals_out, newshape
+    finally:
+        lib.oracle_omp_free(ctypes.byref(out))

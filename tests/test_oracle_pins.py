@@ -97,3 +97,24 @@ def test_dense_kernels_errors_and_empty():
     assert oracle.dot(np.zeros(0), np.zeros(0)) == 0.0
     assert oracle.matvec(np.zeros((3, 0)), np.zeros(0)).tolist() == [0.0, 0.0, 0.0]
     assert oracle.matvec(np.zeros((0, 4)), np.ones(4)).shape == (0,)
+
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 8])
+def test_parallel_statement_is_bit_identical(threads):
+    """The OpenMP statement (the benchmark's multi-core CPU baseline) returns
+    the one-core oracle's result bit for bit: same terms, same order, same
+    compensated sums."""
+    for seed in range(12):
+        g = np.random.default_rng(900 + seed)
+        d = 2 + seed % 4
+        shape = tuple(int(x) for x in g.integers(2, 9, size=d))
+        nnz = int(g.integers(0, 3000))
+        subs = np.stack([g.integers(0, n, size=nnz) for n in shape], axis=1).astype(np.int64)
+        vals = g.uniform(-1, 1, size=nnz)
+        modes = sorted(g.choice(d, size=int(g.integers(1, d + 1)), replace=False).tolist())
+        vecs = [g.uniform(-1, 1, size=shape[m]) for m in modes]
+        for dense in (False, True):
+            a = oracle.ttv(subs, vals, shape, modes, vecs, dense=dense)
+            b = oracle.ttv_parallel(subs, vals, shape, modes, vecs, dense=dense, threads=threads)
+            assert a[2] == b[2]
+            assert np.array_equal(a[1], b[1]) and (dense or np.array_equal(a[0], b[0])), (seed, dense)
