@@ -561,7 +561,23 @@ static int execute(const Plan& pl, ttv_out* out, const ttv_opts* o, cudaStream_t
     layout(pl, a, w);
     StreamDesc p = p0;
     p.status = w.status;
-    cudaMemsetAsync(w.status, 0, sizeof(Status), stream);
+    // The binary64 dense path only raises error flags, rarely: its kernels
+    // then write them straight into the call's pinned status block (zeroed
+    // on the host above), which saves a reset and a copy on the stream.
+    // Graph captures keep the reset and the copy inside the graph.
+    bool direct_status = false;
+    if (pl.path == TTV_PATH_DENSE && !pl.use_fx && !pl.want_presence && p.nnz > 0 && !st->borrowed_status) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        void* dp = nullptr;
+        if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
+            cudaHostGetDevicePointer(&dp, st->hstatus, 0) == cudaSuccess && dp) {
+            p.status = static_cast<Status*>(dp);
+            direct_status = true;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (!direct_status) cudaMemsetAsync(w.status, 0, sizeof(Status), stream);
 
     double* ovals = static_cast<double*>(out->vals);
     if (p.nnz == 0) {
@@ -604,7 +620,8 @@ static int execute(const Plan& pl, ttv_out* out, const ttv_opts* o, cudaStream_t
         st->dense_out = 1;
         out->nnz = 1;
     }
-    e = cudaMemcpyAsync(st->hstatus, w.status, sizeof(Status), cudaMemcpyDeviceToHost, stream);
+    e = direct_status ? cudaSuccess
+                      : cudaMemcpyAsync(st->hstatus, w.status, sizeof(Status), cudaMemcpyDeviceToHost, stream);
     if (own_ws) cudaFreeAsync(ws, stream);
     if (e != cudaSuccess) return cuda_fail(e, "status copy");
     e = cudaGetLastError();
