@@ -439,6 +439,20 @@ static size_t workspace_bytes(const Plan& pl) {
     return a.off;
 }
 
+// The device address of the call's pinned status block, or nullptr where the
+// status must stay in device memory: inside a graph capture (the graph
+// keeps its own reset and copy) or for a batch's borrowed block.
+static Status* direct_status(OutState* st, cudaStream_t stream) {
+    if (st->borrowed_status) return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    void* dp = nullptr;
+    if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
+        cudaHostGetDevicePointer(&dp, st->hstatus, 0) == cudaSuccess && dp)
+        return static_cast<Status*>(dp);
+    cudaGetLastError();
+    return nullptr;
+}
+
 // pyttb's conversion (Sec. 3.3): a sparse result with more than half of its
 // cells present becomes a dense array.  Library-owned results move to a new
 // dense buffer; a caller's value buffer is reused when it holds every cell,
@@ -561,23 +575,15 @@ static int execute(const Plan& pl, ttv_out* out, const ttv_opts* o, cudaStream_t
     layout(pl, a, w);
     StreamDesc p = p0;
     p.status = w.status;
-    // The binary64 dense path only raises error flags, rarely: its kernels
-    // then write them straight into the call's pinned status block (zeroed
-    // on the host above), which saves a reset and a copy on the stream.
-    // Graph captures keep the reset and the copy inside the graph.
-    bool direct_status = false;
-    if (pl.path == TTV_PATH_DENSE && !pl.use_fx && !pl.want_presence && p.nnz > 0 && !st->borrowed_status) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        void* dp = nullptr;
-        if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
-            cudaHostGetDevicePointer(&dp, st->hstatus, 0) == cudaSuccess && dp) {
-            p.status = static_cast<Status*>(dp);
-            direct_status = true;
-        } else {
-            cudaGetLastError();
-        }
-    }
-    if (!direct_status) cudaMemsetAsync(w.status, 0, sizeof(Status), stream);
+    // Paths whose kernels touch the status only rarely (error flags) or once
+    // (the result count) write it straight into the call's pinned status
+    // block (zeroed on the host above): no reset and no copy on the stream.
+    const bool light_status = (pl.path == TTV_PATH_DENSE && !pl.use_fx && !pl.want_presence) ||
+                              (pl.path == TTV_PATH_SORT && !pl.compensated);
+    Status* dstat = (light_status && p.nnz > 0) ? direct_status(st, stream) : nullptr;
+    const bool direct_st = dstat != nullptr;
+    if (direct_st) p.status = dstat;
+    else cudaMemsetAsync(w.status, 0, sizeof(Status), stream);
 
     double* ovals = static_cast<double*>(out->vals);
     if (p.nnz == 0) {
@@ -606,22 +612,22 @@ static int execute(const Plan& pl, ttv_out* out, const ttv_opts* o, cudaStream_t
         } else {
             launch_keys_terms(p, sb.keys[0], sb.vals[0], stream);
         }
-        const int cur = radix_sort_pairs(sb, p.nnz, pl.key_bits, w.status, stream, nullptr, vec);
+        const int cur = radix_sort_pairs(sb, p.nnz, pl.key_bits, p.status, stream, nullptr, vec);
         if (pl.dense_out) cudaMemsetAsync(ovals, 0, (size_t)pl.cap_vals * sizeof(double), stream);
         SegOut so{out->subs, ovals, cap_rows_eff, pl.dense_out, pl.compensated};
         if (pl.compensated)
             launch_seg_reduce(sb.keys[cur], sb.vals[cur], p.nnz, w.seg_start, w.seg_lookback, w.seg_ticket,
                               w.long_list, p, so, w.status, stream);
         else
-            launch_reduce_by_key(sb.keys[cur], sb.vals[cur], p.nnz, w.rbk_state, p, so, w.status, stream);
+            launch_reduce_by_key(sb.keys[cur], sb.vals[cur], p.nnz, w.rbk_state, p, so, p.status, stream);
     }
     if (pl.order0) {
         // scalar result: nnz 1 whatever the input
         st->dense_out = 1;
         out->nnz = 1;
     }
-    e = direct_status ? cudaSuccess
-                      : cudaMemcpyAsync(st->hstatus, w.status, sizeof(Status), cudaMemcpyDeviceToHost, stream);
+    e = direct_st ? cudaSuccess
+                  : cudaMemcpyAsync(st->hstatus, w.status, sizeof(Status), cudaMemcpyDeviceToHost, stream);
     if (own_ws) cudaFreeAsync(ws, stream);
     if (e != cudaSuccess) return cuda_fail(e, "status copy");
     e = cudaGetLastError();
@@ -717,8 +723,12 @@ static int execute_prepared(const ttv_prepared* h, const void* const* vecs, ttv_
     Status* status = a.take<Status>(1);
     void* state = a.take<char>(rbk_state_bytes(h->nnz));
     StreamDesc p = p0;
+    // the reduce-by-key writes the result count once and raises flags only on
+    // errors: straight into the call's pinned status block when possible
+    Status* dstat = h->nnz > 0 ? direct_status(st, stream) : nullptr;
+    if (dstat) status = dstat;
+    else cudaMemsetAsync(status, 0, sizeof(Status), stream);
     p.status = status;
-    cudaMemsetAsync(status, 0, sizeof(Status), stream);
     double* ovals = static_cast<double*>(out->vals);
     if (dense_out) cudaMemsetAsync(ovals, 0, (size_t)std::max<int64_t>(cap_vals, 1) * sizeof(double), stream);
     if (h->nnz > 0) {
@@ -741,7 +751,7 @@ static int execute_prepared(const ttv_prepared* h, const void* const* vecs, ttv_
         st->dense_out = 1;
         out->nnz = 1;
     }
-    e = cudaMemcpyAsync(st->hstatus, status, sizeof(Status), cudaMemcpyDeviceToHost, stream);
+    e = dstat ? cudaSuccess : cudaMemcpyAsync(st->hstatus, status, sizeof(Status), cudaMemcpyDeviceToHost, stream);
     if (own_ws) cudaFreeAsync(ws, stream);
     if (e != cudaSuccess) return cuda_fail(e, "status copy");
     e = cudaGetLastError();
