@@ -291,8 +291,10 @@ int ttv_tune_lookup(const ttv_tensor *t, const int32_t *modes, int32_t n_v, cons
  * ttv_multi, TTV_ERR_UNSUPPORTED for nnz >= 2^30 or a contracted mode of
  * 2^31 or more entries.  ttv_prepared_run takes the vectors in the order of
  * the modes given to ttv_prepare (vec_lens may be NULL; else each must equal
- * its mode size), opts as ttv_multi (fmt, workspace, async; accum must be
- * TTV_ACCUM_FP64, path is ignored), and fills `out` like ttv_multi: for a
+ * its mode size), opts as ttv_multi (fmt, workspace, async; accum
+ * TTV_ACCUM_FP64, or TTV_ACCUM_COMPENSATED: every run sum then carries a
+ * Neumaier error term through all stages and is rounded once; path is
+ * ignored), and fills `out` like ttv_multi: for a
  * sparse result nnz_out rows (ttv_prepared_info), for a dense one
  * prod(shape[R]) values.  Runs on one handle may overlap on different
  * streams; ttv_prepared_free synchronises the device and releases it. */
@@ -387,8 +389,10 @@ int ttv_server_register(ttv_server *server, const ttv_tensor *t, int32_t *tensor
 /* Prepares registered tensor `tensor_id` for TTVs along exactly the modes
  * given (see ttv_prepare; the layout counts against the budget until the
  * server is destroyed).  Later requests on that tensor with the same set of
- * modes (any order), fp64 accumulation and path AUTO run on the prepared
- * layout: results identical to the sort path, no sort passes.  Synchronous;
+ * modes (any order), path AUTO, no determinism request and fp64 or
+ * compensated accumulation run on the prepared layout with no sort passes
+ * (fp64: results identical to the sort path; compensated: the prepared
+ * run's compensated sums, within the same tolerance).  Synchronous;
  * TTV_ERR_BUDGET if the layout does not fit, errors of ttv_prepare
  * otherwise.  May be called while requests run. */
 int ttv_server_prepare(ttv_server *server, int32_t tensor_id, const int32_t *modes, int32_t n_v);

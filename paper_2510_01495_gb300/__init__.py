@@ -432,7 +432,8 @@ class Prepared:
         _check(self._lib, self._lib.ttv_prepared_workspace_size(h, ctypes.byref(ws)))
         self.workspace_bytes = int(ws.value)
 
-    def run(self, vecs, *, fmt="sparse", out_subs=None, out_vals=None, workspace=None, stream=None) -> Result:
+    def run(self, vecs, *, fmt="sparse", accum="fp64", out_subs=None, out_vals=None, workspace=None,
+            stream=None) -> Result:
         if self._h is None:
             raise RuntimeError("prepared tensor released")
         if len(vecs) != len(self.modes):
@@ -456,7 +457,7 @@ class Prepared:
             out_vals = torch.empty(max(1, ncells if dense else self.nnz_out), dtype=torch.float64, device=self.device)
         if out_subs is None and not dense:
             out_subs = torch.empty((max(1, self.nnz_out), self.order), dtype=torch.int64, device=self.device)
-        o = make_opts(fmt=fmt, workspace=workspace)
+        o = make_opts(fmt=fmt, accum=accum, workspace=workspace)
         res = Out()
         res.vals = out_vals.data_ptr()
         res.vals_capacity = out_vals.numel()

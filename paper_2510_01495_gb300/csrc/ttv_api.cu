@@ -743,7 +743,7 @@ static int execute_prepared(const ttv_prepared* h, const void* const* vecs, ttv_
                 terms.vec[j] = vecs[h->arg_of[j]];
                 ++j;
             }
-        SegOut so{out->subs, ovals, cap_rows_eff, dense_out ? 1 : 0, 0};
+        SegOut so{out->subs, ovals, cap_rows_eff, dense_out ? 1 : 0, o->accum == TTV_ACCUM_COMPENSATED ? 1 : 0};
         launch_reduce_by_key_prepared(reinterpret_cast<const uint8_t*>(h->head_bits), h->row_keys, terms, h->nnz,
                                       state, p, so, status, stream);
     }
@@ -1258,8 +1258,8 @@ int ttv_prepared_run(const ttv_prepared* h, const void* const* vecs, const int64
     ttv_opts_init(&def);
     const ttv_opts* o = opts ? opts : &def;
     if (o->fmt < TTV_OUT_SPARSE || o->fmt > TTV_OUT_AUTO) return fail(TTV_ERR_ARG, "bad output format");
-    if (o->accum != TTV_ACCUM_FP64)
-        return fail(TTV_ERR_UNSUPPORTED, "prepared tensors accumulate in binary64 (deterministic order)");
+    if (o->accum != TTV_ACCUM_FP64 && o->accum != TTV_ACCUM_COMPENSATED)
+        return fail(TTV_ERR_UNSUPPORTED, "prepared tensors accumulate in binary64, plain or compensated");
     const StreamDesc& p0 = h->plan.desc;
     int j = 0;
     for (int m = 0; m < p0.d; ++m)

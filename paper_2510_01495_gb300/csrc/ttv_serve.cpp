@@ -144,7 +144,8 @@ void start(ttv_server* s, Slot& sl, const std::shared_ptr<Request>& r) {
         std::lock_guard<std::mutex> g(s->mu);
         t = s->tensors[(size_t)r->tensor];
     }
-    if (r->opts.accum == TTV_ACCUM_FP64 && r->opts.path == TTV_PATH_AUTO) {
+    if ((r->opts.accum == TTV_ACCUM_FP64 || r->opts.accum == TTV_ACCUM_COMPENSATED) &&
+        r->opts.path == TTV_PATH_AUTO && !r->opts.deterministic) {
         uint32_t mask = 0;
         for (int32_t m : r->modes) mask |= 1u << m;
         for (auto& pm : t.prepared)

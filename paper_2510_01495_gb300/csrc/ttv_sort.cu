@@ -484,16 +484,35 @@ constexpr int kRbkItems = 8;
 constexpr int kRbkTile = kRbkThreads * kRbkItems;
 constexpr int kRbkScanThreads = 1024;
 
-struct RbkSum {                  // a summary: value first for alignment
+struct RbkSum {                  // a summary: values first for alignment
     double val;
+    double comp;                 // compensated sums: the running error term (0 otherwise)
     uint32_t cnt;
     uint32_t flag;
 };
 
-__device__ __forceinline__ void seg_combine(uint32_t ca, uint32_t fa, double va, uint32_t& cb, uint32_t& fb,
-                                            double& vb) {
+// s + c += x with Neumaier's correction
+__device__ __forceinline__ void nm_add(double& s, double& c, double x) {
+    const double t = s + x;
+    c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
+// (ca, fa, va, ka) . (cb, fb, vb, kb) -> b; kComp carries the error terms k
+template <bool kComp>
+__device__ __forceinline__ void seg_combine(uint32_t ca, uint32_t fa, double va, double ka, uint32_t& cb,
+                                            uint32_t& fb, double& vb, double& kb) {
     cb = ca + cb;
-    vb = fb ? vb : va + vb;
+    if constexpr (kComp) {
+        if (!fb) {
+            double sv = va, sk = ka;
+            nm_add(sv, sk, vb);
+            vb = sv;
+            kb = sk + kb;
+        }
+    } else {
+        vb = fb ? vb : va + vb;
+    }
     fb = fa | fb;
 }
 
@@ -508,6 +527,7 @@ struct RbkPairs {
     uint32_t heads, cnt, flag;
     double open;
     double first_done;           // done[] at this thread's first head (0 when it has none)
+    double open_k, first_k;      // compensated sums: error terms of open and first_done
 };
 
 // Terms of the sort path: stored next to the sorted keys.
@@ -646,7 +666,7 @@ __device__ __forceinline__ uint32_t rbk_heads(const H& hd, int64_t n, int64_t g0
     }
 }
 
-template <class H, class Src>
+template <bool kComp, class H, class Src>
 __device__ __forceinline__ void rbk_load(const H& hd, const Src& src, int64_t n, int64_t tile, RbkPairs& r) {
     r.g0 = tile * kRbkTile + (int64_t)threadIdx.x * kRbkItems;
     r.nmine = (int)max((int64_t)0, min((int64_t)kRbkItems, n - r.g0));
@@ -657,23 +677,32 @@ __device__ __forceinline__ void rbk_load(const H& hd, const Src& src, int64_t n,
         r.prev0 = 0;
         r.cnt = __popc(r.heads);
         r.flag = r.heads != 0;
-        double acc = 0.0;
+        double acc = 0.0, ak = 0.0;
         r.first_done = 0.0;
+        r.first_k = 0.0;
         const int fh = r.heads ? __ffs(r.heads) - 1 : kRbkItems;
 #pragma unroll
         for (int i = 0; i < kRbkItems; ++i) {
             r.done[i] = 0.0;
             if (i < r.nmine) {
                 if ((r.heads >> i) & 1u) {
-                    r.done[i] = acc;
-                    if (i == fh) r.first_done = acc;
+                    if constexpr (kComp) {
+                        r.done[i] = acc + ak;       // a run closed inside the range: final value
+                        if (i == fh) { r.first_done = acc; r.first_k = ak; }
+                        ak = 0.0;
+                    } else {
+                        r.done[i] = acc;
+                        if (i == fh) r.first_done = acc;
+                    }
                     acc = r.v[i];
                 } else {
-                    acc = acc + r.v[i];
+                    if constexpr (kComp) nm_add(acc, ak, r.v[i]);
+                    else acc = acc + r.v[i];
                 }
             }
         }
         r.open = acc;
+        r.open_k = ak;
         return;
     }
     const uint64_t* keys = key_array(hd);
@@ -694,27 +723,36 @@ __device__ __forceinline__ void rbk_load(const H& hd, const Src& src, int64_t n,
     r.heads = 0;
     r.cnt = 0;
     r.flag = 0;
-    double acc = 0.0;
+    double acc = 0.0, ak = 0.0;
     uint64_t prev = r.prev0;
     r.first_done = 0.0;
+    r.first_k = 0.0;
 #pragma unroll
     for (int i = 0; i < kRbkItems; ++i) {
         r.done[i] = 0.0;
         if (i < r.nmine) {
             if (r.k[i] != prev || r.g0 + i == 0) {
-                if (!r.flag) r.first_done = acc;
+                if constexpr (kComp) {
+                    if (!r.flag) { r.first_done = acc; r.first_k = ak; }
+                    r.done[i] = acc + ak;
+                    ak = 0.0;
+                } else {
+                    if (!r.flag) r.first_done = acc;
+                    r.done[i] = acc;
+                }
                 r.heads |= 1u << i;
                 ++r.cnt;
                 r.flag = 1;
-                r.done[i] = acc;
                 acc = r.v[i];
             } else {
-                acc = acc + r.v[i];
+                if constexpr (kComp) nm_add(acc, ak, r.v[i]);
+                else acc = acc + r.v[i];
             }
             prev = r.k[i];
         }
     }
     r.open = acc;
+    r.open_k = ak;
 }
 
 // Block scan of the thread summaries: each thread gets its exclusive prefix
@@ -723,69 +761,82 @@ struct RbkScanSmem {
     uint32_t cnt[kRbkThreads / 32];
     uint32_t flag[kRbkThreads / 32];
     double val[kRbkThreads / 32];
+    double kv[kRbkThreads / 32];
     uint32_t pcnt[kRbkThreads / 32 + 1];   // exclusive prefix of warp w; [8]: the tile total
     uint32_t pflag[kRbkThreads / 32 + 1];
     double pval[kRbkThreads / 32 + 1];
+    double pk[kRbkThreads / 32 + 1];
 };
 
+template <bool kComp>
 __device__ __forceinline__ void rbk_block_scan(const RbkPairs& r, RbkScanSmem& ss, uint32_t& xc, uint32_t& xf,
-                                               double& xv, uint32_t& tc, uint32_t& tf, double& tv) {
+                                               double& xv, double& xk, uint32_t& tc, uint32_t& tf, double& tv,
+                                               double& tk) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t c = r.cnt, f = r.flag;
-    double v = r.open;
+    double v = r.open, k = kComp ? r.open_k : 0.0;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const uint32_t c2 = __shfl_up_sync(0xffffffffu, c, off);
         const uint32_t f2 = __shfl_up_sync(0xffffffffu, f, off);
         const double v2 = __shfl_up_sync(0xffffffffu, v, off);
-        if (lane >= off) seg_combine(c2, f2, v2, c, f, v);
+        const double k2 = kComp ? __shfl_up_sync(0xffffffffu, k, off) : 0.0;
+        if (lane >= off) seg_combine<kComp>(c2, f2, v2, k2, c, f, v, k);
     }
     if (lane == 31) {
         ss.cnt[warp] = c;
         ss.flag[warp] = f;
         ss.val[warp] = v;
+        if (kComp) ss.kv[warp] = k;
     }
     xc = __shfl_up_sync(0xffffffffu, c, 1);
     xf = __shfl_up_sync(0xffffffffu, f, 1);
     xv = __shfl_up_sync(0xffffffffu, v, 1);
-    if (lane == 0) { xc = 0; xf = 0; xv = 0.0; }
+    xk = kComp ? __shfl_up_sync(0xffffffffu, k, 1) : 0.0;
+    if (lane == 0) { xc = 0; xf = 0; xv = 0.0; xk = 0.0; }
     __syncthreads();
     // warp prefixes, folded left to right over the 8 warps by one thread
     if (threadIdx.x == 0) {
         uint32_t pc = ss.cnt[0], pf = ss.flag[0];
-        double pv = ss.val[0];
+        double pv = ss.val[0], pk = kComp ? ss.kv[0] : 0.0;
 #pragma unroll
         for (int w = 1; w < kRbkThreads / 32; ++w) {
             ss.pcnt[w] = pc;
             ss.pflag[w] = pf;
             ss.pval[w] = pv;
+            if (kComp) ss.pk[w] = pk;
             uint32_t cw = ss.cnt[w], fw = ss.flag[w];
-            double vw = ss.val[w];
-            seg_combine(pc, pf, pv, cw, fw, vw);
+            double vw = ss.val[w], kw = kComp ? ss.kv[w] : 0.0;
+            seg_combine<kComp>(pc, pf, pv, pk, cw, fw, vw, kw);
             pc = cw;
             pf = fw;
             pv = vw;
+            pk = kw;
         }
         ss.pcnt[kRbkThreads / 32] = pc;
         ss.pflag[kRbkThreads / 32] = pf;
         ss.pval[kRbkThreads / 32] = pv;
+        if (kComp) ss.pk[kRbkThreads / 32] = pk;
     }
     __syncthreads();
-    if (warp > 0) seg_combine(ss.pcnt[warp], ss.pflag[warp], ss.pval[warp], xc, xf, xv);
+    if (warp > 0)
+        seg_combine<kComp>(ss.pcnt[warp], ss.pflag[warp], ss.pval[warp], kComp ? ss.pk[warp] : 0.0, xc, xf, xv, xk);
     tc = ss.pcnt[kRbkThreads / 32];
     tf = ss.pflag[kRbkThreads / 32];
     tv = ss.pval[kRbkThreads / 32];
+    tk = kComp ? ss.pk[kRbkThreads / 32] : 0.0;
 }
 
 // A tile's summary needs its head count and the sum of the terms after its
 // last head (all its terms when it has none): only the thread holding the
 // last head and the threads after it form and add terms.  The partial sums
 // are combined in a fixed order (shuffle tree, then warps left to right).
-template <class H, class Src>
+template <bool kComp, class H, class Src>
 __global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles(H hd, Src src, int64_t n, RbkSum* __restrict__ tiles) {
     __shared__ int s_last[kRbkThreads / 32];
     __shared__ uint32_t s_cnt[kRbkThreads / 32];
     __shared__ double s_val[kRbkThreads / 32];
+    __shared__ double s_k[kRbkThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t g0 = (int64_t)blockIdx.x * kRbkTile + (int64_t)tid * kRbkItems;
     const int nmine = (int)max((int64_t)0, min((int64_t)kRbkItems, n - g0));
@@ -805,22 +856,45 @@ __global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles(H hd, Src src, int64_
         last = max(last, s_last[w]);
         cnt += s_cnt[w];
     }
-    double c = 0.0;
+    double c = 0.0, ck = 0.0;
     if (tid >= last && nmine > 0) {
         const int start = tid == last ? 31 - __clz(heads) : 0;   // this thread's last head
         c = src.term(g0 + start);
-        for (int i = start + 1; i < nmine; ++i) c = c + src.term(g0 + i);
+        for (int i = start + 1; i < nmine; ++i) {
+            if constexpr (kComp) nm_add(c, ck, src.term(g0 + i));
+            else c = c + src.term(g0 + i);
+        }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) c = c + __shfl_down_sync(0xffffffffu, c, off);
+    for (int off = 16; off > 0; off >>= 1) {
+        const double oc = __shfl_down_sync(0xffffffffu, c, off);
+        if constexpr (kComp) {
+            const double ok = __shfl_down_sync(0xffffffffu, ck, off);
+            nm_add(c, ck, oc);
+            ck = ck + ok;
+        } else {
+            c = c + oc;
+        }
+    }
     __syncthreads();
-    if (lane == 0) s_val[warp] = c;
+    if (lane == 0) {
+        s_val[warp] = c;
+        if (kComp) s_k[warp] = ck;
+    }
     __syncthreads();
     if (tid == 0) {
-        double v = 0.0;
-        for (int w = max(last, 0) >> 5; w < kRbkThreads / 32; ++w) v = v + s_val[w];
+        double v = 0.0, vk = 0.0;
+        for (int w = max(last, 0) >> 5; w < kRbkThreads / 32; ++w) {
+            if constexpr (kComp) {
+                nm_add(v, vk, s_val[w]);
+                vk = vk + s_k[w];
+            } else {
+                v = v + s_val[w];
+            }
+        }
         RbkSum t;
         t.val = v;
+        t.comp = vk;
         t.cnt = cnt;
         t.flag = last >= 0;
         tiles[blockIdx.x] = t;
@@ -831,6 +905,7 @@ __global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles(H hd, Src src, int64_
 // group (ingroup[t]) and the group's summary (groups[g]).
 constexpr int kRbkGroup = 32;
 
+template <bool kComp>
 __global__ void __launch_bounds__(256) k_rbk_groups(const RbkSum* __restrict__ tiles, int64_t ntiles,
                                                     RbkSum* __restrict__ ingroup, RbkSum* __restrict__ groups,
                                                     int64_t ngroups) {
@@ -838,33 +913,51 @@ __global__ void __launch_bounds__(256) k_rbk_groups(const RbkSum* __restrict__ t
     const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (g >= ngroups) return;
     const int64_t t = g * kRbkGroup + lane;
-    RbkSum a = t < ntiles ? tiles[t] : RbkSum{0.0, 0u, 0u};
+    RbkSum a = t < ntiles ? tiles[t] : RbkSum{0.0, 0.0, 0u, 0u};
     uint32_t c = a.cnt, f = a.flag;
-    double v = a.val;
+    double v = a.val, k = kComp ? a.comp : 0.0;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const uint32_t c2 = __shfl_up_sync(0xffffffffu, c, off);
         const uint32_t f2 = __shfl_up_sync(0xffffffffu, f, off);
         const double v2 = __shfl_up_sync(0xffffffffu, v, off);
-        if (lane >= off) seg_combine(c2, f2, v2, c, f, v);
+        const double k2 = kComp ? __shfl_up_sync(0xffffffffu, k, off) : 0.0;
+        if (lane >= off) seg_combine<kComp>(c2, f2, v2, k2, c, f, v, k);
     }
     uint32_t xc = __shfl_up_sync(0xffffffffu, c, 1);
     uint32_t xf = __shfl_up_sync(0xffffffffu, f, 1);
     double xv = __shfl_up_sync(0xffffffffu, v, 1);
-    if (lane == 0) { xc = 0; xf = 0; xv = 0.0; }
-    if (t < ntiles) ingroup[t] = RbkSum{xv, xc, xf};
-    if (lane == 31) groups[g] = RbkSum{v, c, f};
+    double xk = kComp ? __shfl_up_sync(0xffffffffu, k, 1) : 0.0;
+    if (lane == 0) { xc = 0; xf = 0; xv = 0.0; xk = 0.0; }
+    if (t < ntiles) ingroup[t] = RbkSum{xv, xk, xc, xf};
+    if (lane == 31) groups[g] = RbkSum{v, k, c, f};
 }
 
 // Exclusive scan of the group summaries; gprefix[g] = open value entering
 // group g, gheads[g] = heads before it; the total head count is the result
 // size.
+// (va, ka) then (vb, kb) into b: the compensated left-to-right sum of two
+// partial sums; plain addition without kComp.
+template <bool kComp>
+__device__ __forceinline__ void cat_sum(double va, double ka, double& vb, double& kb) {
+    if constexpr (kComp) {
+        double sv = va, sk = ka;
+        nm_add(sv, sk, vb);
+        vb = sv;
+        kb = sk + kb;
+    } else {
+        vb = va + vb;
+    }
+}
+
+template <bool kComp>
 __global__ void __launch_bounds__(kRbkScanThreads) k_rbk_scan(const RbkSum* __restrict__ groups, int64_t ngroups,
                                                               RbkSum* __restrict__ gprefix,
                                                               unsigned long long* __restrict__ gheads,
                                                               Status* st) {
     __shared__ uint32_t s_flag[kRbkScanThreads / 32];
     __shared__ double s_val[kRbkScanThreads / 32];
+    __shared__ double s_k[kRbkScanThreads / 32];
     __shared__ unsigned long long s_base[kRbkScanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t per = (ngroups + kRbkScanThreads - 1) / kRbkScanThreads;
@@ -872,25 +965,34 @@ __global__ void __launch_bounds__(kRbkScanThreads) k_rbk_scan(const RbkSum* __re
     // chunk summary, left to right (head counts in 64 bits)
     unsigned long long cc = 0;
     uint32_t cf = 0;
-    double cv = 0.0;
+    double cv = 0.0, ck = 0.0;
     for (int64_t t = lo; t < hi; ++t) {
         const RbkSum a = groups[t];
         cc += a.cnt;
-        cv = a.flag ? a.val : cv + a.val;
+        if (a.flag) {
+            cv = a.val;
+            ck = kComp ? a.comp : 0.0;
+        } else {
+            double av = a.val, ak = kComp ? a.comp : 0.0;
+            cat_sum<kComp>(cv, ck, av, ak);
+            cv = av;
+            ck = ak;
+        }
         cf |= a.flag;
     }
     // exclusive scan over chunks: counts by warp sums, values by a fixed tree
     unsigned long long c = cc;
     uint32_t f = cf;
-    double v = cv;
+    double v = cv, k = ck;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const unsigned long long c2 = __shfl_up_sync(0xffffffffu, c, off);
         const uint32_t f2 = __shfl_up_sync(0xffffffffu, f, off);
         const double v2 = __shfl_up_sync(0xffffffffu, v, off);
+        const double k2 = kComp ? __shfl_up_sync(0xffffffffu, k, off) : 0.0;
         if (lane >= off) {
             c = c2 + c;
-            v = f ? v : v2 + v;
+            if (!f) cat_sum<kComp>(v2, k2, v, k);
             f = f2 | f;
         }
     }
@@ -898,27 +1000,46 @@ __global__ void __launch_bounds__(kRbkScanThreads) k_rbk_scan(const RbkSum* __re
         s_base[warp] = c;
         s_flag[warp] = f;
         s_val[warp] = v;
+        s_k[warp] = k;
     }
     unsigned long long xc = __shfl_up_sync(0xffffffffu, c, 1);
     uint32_t xf = __shfl_up_sync(0xffffffffu, f, 1);
     double xv = __shfl_up_sync(0xffffffffu, v, 1);
-    if (lane == 0) { xc = 0; xf = 0; xv = 0.0; }
+    double xk = kComp ? __shfl_up_sync(0xffffffffu, k, 1) : 0.0;
+    if (lane == 0) { xc = 0; xf = 0; xv = 0.0; xk = 0.0; }
     __syncthreads();
     unsigned long long pc = 0;
-    double pv = 0.0;
+    double pv = 0.0, pk = 0.0;
     for (int w = 0; w < warp; ++w) {
         pc = pc + s_base[w];
-        pv = s_flag[w] ? s_val[w] : pv + s_val[w];
+        if (s_flag[w]) {
+            pv = s_val[w];
+            pk = kComp ? s_k[w] : 0.0;
+        } else {
+            double wv = s_val[w], wk = kComp ? s_k[w] : 0.0;
+            cat_sum<kComp>(pv, pk, wv, wk);
+            pv = wv;
+            pk = wk;
+        }
     }
     // this chunk's exclusive prefix = warp prefix . lane-exclusive
     unsigned long long rc = pc + xc;
-    double rv = xf ? xv : pv + xv;
+    double rv = xv, rk = xk;
+    if (!xf) cat_sum<kComp>(pv, pk, rv, rk);
     for (int64_t t = lo; t < hi; ++t) {
-        gprefix[t] = RbkSum{rv, 0u, 0u};
+        gprefix[t] = RbkSum{rv, rk, 0u, 0u};
         gheads[t] = rc;
         const RbkSum a = groups[t];
         rc += a.cnt;
-        rv = a.flag ? a.val : rv + a.val;
+        if (a.flag) {
+            rv = a.val;
+            rk = kComp ? a.comp : 0.0;
+        } else {
+            double av = a.val, ak = kComp ? a.comp : 0.0;
+            cat_sum<kComp>(rv, rk, av, ak);
+            rv = av;
+            rk = ak;
+        }
     }
     if (hi == ngroups && lo < hi) st->nnz_out = rc;
 }
@@ -929,7 +1050,7 @@ struct RbkEmitSmem {
     RbkScanSmem ss;
 };
 
-template <class H, class Src>
+template <bool kComp, class H, class Src>
 __global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(H hd, Src src, int64_t n,
                                                              const RbkSum* __restrict__ ingroup,
                                                              const RbkSum* __restrict__ gprefix,
@@ -940,17 +1061,19 @@ __global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(H hd, Src src, int6
     const int64_t tile = blockIdx.x;
     const int64_t ntiles = (n + kRbkTile - 1) / kRbkTile;
     RbkPairs r;
-    rbk_load(hd, src, n, tile, r);
+    rbk_load<kComp>(hd, src, n, tile, r);
     uint32_t xc, xf, tc, tf;
-    double xv, tv;
-    rbk_block_scan(r, sm.ss, xc, xf, xv, tc, tf, tv);
+    double xv, xk, tv, tk;
+    rbk_block_scan<kComp>(r, sm.ss, xc, xf, xv, xk, tc, tf, tv, tk);
     // open value entering the tile: group prefix . in-group prefix
     const RbkSum ig = ingroup[tile];
     const int64_t g = tile / kRbkGroup;
-    const double carry = ig.flag ? ig.val : gprefix[g].val + ig.val;
+    double carry = ig.val, carry_k = kComp ? ig.comp : 0.0;
+    if (!ig.flag) cat_sum<kComp>(gprefix[g].val, kComp ? gprefix[g].comp : 0.0, carry, carry_k);
     const unsigned long long hb = gheads[g] + ig.cnt;
     // value of the run open when this thread's range starts
-    const double base = xf ? xv : carry + xv;
+    double base = xv, base_k = xk;
+    if (!xf) cat_sum<kComp>(carry, carry_k, base, base_k);
     // a head at tile-local head index h closes the segment at row h - first
     // of this tile (first = 1 in tile 0, whose first head closes nothing);
     // the sum of a run that starts inside this thread's range was formed by
@@ -961,7 +1084,9 @@ __global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(H hd, Src src, int6
     // the first head closes the run open at the range start: its sum is
     // base + the part formed here (one add per thread, not per head)
     const int fh = r.heads ? __ffs(r.heads) - 1 : kRbkItems;
-    const double closed_first = base + r.first_done;
+    double closed_first = r.first_done, closed_first_k = kComp ? r.first_k : 0.0;
+    cat_sum<kComp>(base, base_k, closed_first, closed_first_k);
+    if (kComp) closed_first = closed_first + closed_first_k;
 #pragma unroll
     for (int i = 0; i < kRbkItems; ++i) {
         if (i < r.nmine) {
@@ -978,7 +1103,9 @@ __global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(H hd, Src src, int6
     const bool last_tile = tile == ntiles - 1;
     if (r.nmine > 0 && r.g0 + r.nmine == n) {   // the last pair closes the last segment
         if constexpr (!H::kBits) sm.row_key[h - first] = prev;
-        sm.row_val[h - first] = r.flag ? r.open : base + r.open;
+        double lv = r.open, lk = kComp ? r.open_k : 0.0;
+        if (!r.flag) cat_sum<kComp>(base, base_k, lv, lk);
+        sm.row_val[h - first] = kComp ? lv + lk : lv;
     }
     __syncthreads();
     const int nrows = (int)tc - first + (last_tile ? 1 : 0);
@@ -1031,7 +1158,7 @@ size_t rbk_state_bytes(int64_t n) {
            (size_t)ngroups * (2 * sizeof(RbkSum) + sizeof(unsigned long long)) + 512;
 }
 
-template <class H, class Src>
+template <bool kComp, class H, class Src>
 static void rbk_launch(const H& hd, const Src& src, int64_t n, void* state, const StreamDesc& p, const SegOut& o,
                        Status* st, cudaStream_t stream) {
     if (n <= 0) return;
@@ -1045,25 +1172,26 @@ static void rbk_launch(const H& hd, const Src& src, int64_t n, void* state, cons
     const size_t smem = sizeof(RbkEmitSmem);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_rbk_emit<H, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_rbk_emit<H, Src>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_rbk_emit<kComp, H, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_rbk_emit<kComp, H, Src>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
         attr_set = true;
     }
-    TTV_LAUNCH("rbk_tiles", stream, k_rbk_tiles<H, Src><<<(unsigned)ntiles, kRbkThreads, 0, stream>>>(hd, src, n, tiles));
+    TTV_LAUNCH("rbk_tiles", stream,
+               k_rbk_tiles<kComp, H, Src><<<(unsigned)ntiles, kRbkThreads, 0, stream>>>(hd, src, n, tiles));
     TTV_LAUNCH("rbk_groups", stream,
-               k_rbk_groups<<<(unsigned)((ngroups * 32 + 255) / 256), 256, 0, stream>>>(tiles, ntiles, ingroup, groups,
-                                                                                      ngroups));
+               k_rbk_groups<kComp><<<(unsigned)((ngroups * 32 + 255) / 256), 256, 0, stream>>>(tiles, ntiles, ingroup,
+                                                                                             groups, ngroups));
     TTV_LAUNCH("rbk_scan", stream,
-               k_rbk_scan<<<1, kRbkScanThreads, 0, stream>>>(groups, ngroups, gprefix, gheads, st));
+               k_rbk_scan<kComp><<<1, kRbkScanThreads, 0, stream>>>(groups, ngroups, gprefix, gheads, st));
     TTV_LAUNCH("rbk_emit", stream,
-               k_rbk_emit<H, Src><<<(unsigned)ntiles, kRbkThreads, smem, stream>>>(hd, src, n, ingroup, gprefix,
-                                                                                    gheads, p, o, st));
+               k_rbk_emit<kComp, H, Src><<<(unsigned)ntiles, kRbkThreads, smem, stream>>>(hd, src, n, ingroup,
+                                                                                           gprefix, gheads, p, o, st));
 }
 
 void launch_reduce_by_key(const uint64_t* keys, const double* vals, int64_t n, void* state, const StreamDesc& p,
                           const SegOut& o, Status* st, cudaStream_t stream) {
-    rbk_launch(KeyHeads{keys}, PairTerms{vals}, n, state, p, o, st, stream);
+    rbk_launch<false>(KeyHeads{keys}, PairTerms{vals}, n, state, p, o, st, stream);
 }
 
 // The key of every run of a sorted key array, by run index (vals: any n
@@ -1072,13 +1200,16 @@ void launch_run_keys(const uint64_t* keys, const double* vals, int64_t n, void* 
                      int64_t cap_rows, const StreamDesc& p, Status* st, cudaStream_t stream) {
     SegOut o{nullptr, nullptr, cap_rows, 0, 0};
     o.row_keys = row_keys;
-    rbk_launch(KeyHeads{keys}, PairTerms{vals}, n, state, p, o, st, stream);
+    rbk_launch<false>(KeyHeads{keys}, PairTerms{vals}, n, state, p, o, st, stream);
 }
 
 void launch_reduce_by_key_prepared(const uint8_t* head_bits, const uint64_t* row_keys, const PrepTerms& terms,
                                    int64_t n, void* state, const StreamDesc& p, const SegOut& o, Status* st,
                                    cudaStream_t stream) {
-    rbk_launch(BitHeads{head_bits, row_keys}, PrepTermsDev{terms}, n, state, p, o, st, stream);
+    // o.compensated: the run sums carry a Neumaier error term through every
+    // stage (thread, tile, group, scan) and are rounded once when written
+    if (o.compensated) rbk_launch<true>(BitHeads{head_bits, row_keys}, PrepTermsDev{terms}, n, state, p, o, st, stream);
+    else rbk_launch<false>(BitHeads{head_bits, row_keys}, PrepTermsDev{terms}, n, state, p, o, st, stream);
 }
 
 void launch_seg_reduce(const uint64_t* keys, const double* vals, int64_t n, uint32_t* seg_start,

@@ -99,3 +99,43 @@ def test_prepared_errors_and_empty(cuda_lib):
     r = empty.run([torch.ones(4, dtype=torch.float64, device=dev)], fmt="dense")
     assert r.vals.shape == (3, 5) and float(r.vals.abs().sum()) == 0.0
     empty.close()
+
+
+@pytest.mark.parametrize("case", [
+    ((300, 200, 100), 100_003, [1]),
+    ((30, 20, 10, 5), 20_000, [0, 3]),
+    ((2, 5000, 80), 400_001, [1, 2]),           # two rows of 200 000 nonzeros: runs across many tiles
+])
+def test_prepared_compensated_matches_oracle(cuda_lib, case):
+    shape, nnz, modes = case
+    t = S.sptenrand(61 + nnz, shape, nnz, vals="u11")
+    vecs = [S.vector(61 + nnz, m, shape[m]) for m in modes]
+    subs = t.subs.t().contiguous().t().cuda()
+    dv = [v.cuda() for v in vecs]
+    prep = ttv.Prepared(subs, t.vals.cuda(), shape, modes)
+    r1 = prep.run(dv, accum="compensated")
+    r2 = prep.run(dv, accum="compensated")
+    assert torch.equal(r1.subs, r2.subs) and torch.equal(r1.vals, r2.vals)       # fixed order
+    ref, A = oracle_ttv(t.subs, t.vals, shape, modes, vecs)
+    check_result(r1, ref, A, what=f"prepared compensated {case}")
+    rp = prep.run(dv)                                                             # plain binary64 unchanged
+    rs = ttv.ttv_multi(subs, t.vals.cuda(), shape, modes, dv, path="sort")
+    assert torch.equal(rp.subs, rs.subs) and torch.equal(rp.vals, rs.vals)
+    prep.close()
+
+
+def test_prepared_compensated_recovers_cancelled_terms(cuda_lib):
+    """One result row of 4e5 terms repeating (2^53, 1, -2^53, 1): a plain
+    binary64 sum loses every 1 that meets 2^53, the compensated run sums
+    carry it through the thread, tile, group and scan stages: exactly 2e5."""
+    n = 400_000
+    pattern = np.array([2.0 ** 53, 1.0, -(2.0 ** 53), 1.0])
+    vals = torch.from_numpy(np.tile(pattern, n // 4)).cuda()
+    subs = torch.stack([torch.zeros(n, dtype=torch.int64), torch.arange(n, dtype=torch.int64)], dim=1).cuda()
+    prep = ttv.Prepared(subs, vals, (1, n), [1])
+    x = torch.ones(n, dtype=torch.float64, device="cuda")
+    rc = prep.run([x], accum="compensated")
+    assert rc.vals.cpu().tolist() == [n / 2]
+    (_, ref_vals, _), _ = oracle_ttv(subs.cpu(), vals.cpu(), (1, n), [1], [x.cpu()])
+    assert ref_vals.tolist() == [n / 2]
+    prep.close()
