@@ -22,9 +22,6 @@ void launch_dense(const StreamDesc& p, int want_presence, int compensated, int G
                   uint32_t* pres_partials, double* cell_vals, uint32_t* cell_flags, cudaStream_t stream);
 void launch_compact_cells(const StreamDesc& p, const double* cell_vals, const uint32_t* cell_flags, int64_t cap_rows,
                           int64_t* out_subs, double* out_vals, cudaStream_t stream);
-void launch_seg_reduce(const uint64_t* keys, const double* vals, int64_t n, uint32_t* seg_start,
-                       unsigned long long* lookback, uint32_t* ticket, uint32_t* long_list, const StreamDesc& p,
-                       const SegOut& o, Status* st, cudaStream_t stream);
 size_t rbk_state_bytes(int64_t n);
 void launch_reduce_by_key_prepared(const uint8_t* head_bits, const uint64_t* row_keys, const PrepTerms& terms,
                                    int64_t n, void* state, const StreamDesc& p, const SegOut& o, Status* st,
@@ -379,10 +376,6 @@ struct WsPtrs {
     uint32_t* cell_flags;
     // sort
     SortBuffers sb;
-    uint32_t* seg_start;
-    unsigned long long* seg_lookback;
-    uint32_t* seg_ticket;
-    uint32_t* long_list;
     void* rbk_state;
 };
 
@@ -419,15 +412,7 @@ static void layout(const Plan& pl, Arena& a, WsPtrs& w) {
         w.sb.tickets = a.take<uint32_t>(64);
         w.sb.npass = npass;
         w.sb.ntiles = ntiles;
-        if (pl.compensated) {
-            // compensated sums: runs found first, then summed one run per thread
-            w.seg_start = a.take<uint32_t>(n + 1);
-            w.seg_lookback = a.take<unsigned long long>(ntiles);
-            w.seg_ticket = a.take<uint32_t>(64);
-            w.long_list = a.take<uint32_t>(n);
-        } else {
-            w.rbk_state = a.take<char>(rbk_state_bytes(n));
-        }
+        w.rbk_state = a.take<char>(rbk_state_bytes(n));
     }
     a.off = (a.off + 255) & ~size_t(255);
 }
@@ -579,7 +564,7 @@ static int execute(const Plan& pl, ttv_out* out, const ttv_opts* o, cudaStream_t
     // (the result count) write it straight into the call's pinned status
     // block (zeroed on the host above): no reset and no copy on the stream.
     const bool light_status = (pl.path == TTV_PATH_DENSE && !pl.use_fx && !pl.want_presence) ||
-                              (pl.path == TTV_PATH_SORT && !pl.compensated);
+                              pl.path == TTV_PATH_SORT;
     Status* dstat = (light_status && p.nnz > 0) ? direct_status(st, stream) : nullptr;
     const bool direct_st = dstat != nullptr;
     if (direct_st) p.status = dstat;
@@ -615,11 +600,7 @@ static int execute(const Plan& pl, ttv_out* out, const ttv_opts* o, cudaStream_t
         const int cur = radix_sort_pairs(sb, p.nnz, pl.key_bits, p.status, stream, nullptr, vec);
         if (pl.dense_out) cudaMemsetAsync(ovals, 0, (size_t)pl.cap_vals * sizeof(double), stream);
         SegOut so{out->subs, ovals, cap_rows_eff, pl.dense_out, pl.compensated};
-        if (pl.compensated)
-            launch_seg_reduce(sb.keys[cur], sb.vals[cur], p.nnz, w.seg_start, w.seg_lookback, w.seg_ticket,
-                              w.long_list, p, so, w.status, stream);
-        else
-            launch_reduce_by_key(sb.keys[cur], sb.vals[cur], p.nnz, w.rbk_state, p, so, p.status, stream);
+        launch_reduce_by_key(sb.keys[cur], sb.vals[cur], p.nnz, w.rbk_state, p, so, p.status, stream);
     }
     if (pl.order0) {
         // scalar result: nnz 1 whatever the input

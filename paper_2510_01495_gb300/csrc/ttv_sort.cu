@@ -11,9 +11,9 @@
 // a global counter, so a tile only waits on tiles that are already running;
 // every wait is bounded and reports kErrTimeout instead of hanging.
 //
-// Stability matters: equal keys keep their input order, so the segmented
-// reduction that follows sums every group in input order and the result is
-// bit-identical from run to run.
+// Stability matters: equal keys keep their input order, so the reduction
+// by key that follows (binary64 or compensated) sums every group in an order
+// fixed by the input alone, and the result is bit-identical from run to run.
 #include <cstdio>
 
 #include "ttv_internal.cuh"
@@ -38,14 +38,6 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
 }
 __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -290,171 +282,6 @@ int radix_sort_pairs(SortBuffers& sb, int64_t n, int bits, Status* st, cudaStrea
         cur ^= 1;
     }
     return cur;
-}
-
-// ---------------------------------------------------------------------------
-// Segmented reduction of sorted pairs.
-//
-// k_seg_heads marks the first pair of every run of equal keys, numbers the
-// runs with a chained scan across tiles and records where each run starts.
-// k_seg_sum sums runs of up to kShortSeg pairs in one thread (in sorted, i.e.
-// input, order) and queues longer runs for k_long_seg, where one warp sums a
-// run with a fixed lane assignment and a fixed shuffle tree.  Both write the
-// result row: the key delinearised into the surviving subscripts, and the sum.
-constexpr int kSegThreads = 256;
-constexpr int kSegItems = 16;
-constexpr int kSegTile = kSegThreads * kSegItems;
-constexpr int kShortSeg = 32;
-constexpr unsigned long long kFlag64Agg = 1ull << 62;
-constexpr unsigned long long kFlag64Inc = 2ull << 62;
-constexpr unsigned long long kCount64Mask = (1ull << 62) - 1;
-
-__global__ void __launch_bounds__(kSegThreads) k_seg_heads(const uint64_t* __restrict__ keys, int64_t n,
-                                                           uint32_t* __restrict__ seg_start,
-                                                           unsigned long long* lookback, uint32_t* ticket,
-                                                           Status* st) {
-    __shared__ uint32_t wt[kSortWarps];
-    __shared__ uint32_t s_tile;
-    __shared__ unsigned long long s_excl;
-    const int tid = threadIdx.x;
-    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    const int64_t base = (int64_t)tile * kSegTile + (int64_t)tid * kSegItems;
-    uint32_t headbits = 0, cnt = 0;
-    uint64_t prev = 0;
-    if (base > 0 && base <= n - 1) prev = keys[base - 1];
-#pragma unroll
-    for (int i = 0; i < kSegItems; ++i) {
-        const int64_t idx = base + i;
-        if (idx < n) {
-            const uint64_t k = keys[idx];
-            if (idx == 0 || k != prev) { headbits |= 1u << i; ++cnt; }
-            prev = k;
-        }
-    }
-    uint32_t tile_total;
-    const uint32_t ex = block_exclusive_scan_256(cnt, wt, tile_total);
-    if (tid == 0) {
-        unsigned long long* my = lookback + tile;
-        unsigned long long excl = 0;
-        if (tile == 0) {
-            st_relaxed64(my, kFlag64Inc | tile_total);
-        } else {
-            st_relaxed64(my, kFlag64Agg | tile_total);
-            int64_t j = (int64_t)tile - 1;
-            while (j >= 0) {
-                unsigned long long val = 0;
-                bool ok = false;
-                for (uint32_t it = 0; it < (1u << 24); ++it) {
-                    val = ld_relaxed64(lookback + j);
-                    if (val & (kFlag64Agg | kFlag64Inc)) { ok = true; break; }
-                    if (it > 32) __nanosleep(32);
-                }
-                if (!ok) { set_error(st, kErrTimeout); break; }
-                excl += val & kCount64Mask;
-                if (val & kFlag64Inc) break;
-                --j;
-            }
-            st_relaxed64(my, kFlag64Inc | (excl + tile_total));
-        }
-        s_excl = excl;
-        const int64_t ntiles = (n + kSegTile - 1) / kSegTile;
-        if ((int64_t)tile == ntiles - 1) {
-            st->nnz_out = excl + tile_total;
-            seg_start[excl + tile_total] = (uint32_t)n;
-        }
-    }
-    __syncthreads();
-    uint32_t g = (uint32_t)s_excl + ex;
-#pragma unroll
-    for (int i = 0; i < kSegItems; ++i)
-        if (headbits & (1u << i)) seg_start[g++] = (uint32_t)(base + i);
-}
-
-
-__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
-    s = a + b;
-    const double bp = s - a;
-    e = (a - (s - bp)) + (b - bp);
-}
-
-__global__ void __launch_bounds__(256) k_seg_sum(const uint64_t* __restrict__ keys, const double* __restrict__ vals,
-                                                 const uint32_t* __restrict__ seg_start, StreamDesc p, SegOut o,
-                                                 uint32_t* __restrict__ long_list, Status* st) {
-    const unsigned long long U = *(volatile unsigned long long*)&st->nnz_out;
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if ((unsigned long long)j >= U) return;
-    if (!o.dense && (unsigned long long)o.cap_rows < U) {
-        if (j == 0) set_error(st, kErrCapacity);
-        return;
-    }
-    const uint32_t s0 = seg_start[j], s1 = seg_start[j + 1];
-    const uint64_t key = keys[s0];
-    if (!o.dense) delinearise(p, key, o.subs + j * p.nr);
-    if (s1 - s0 > (uint32_t)kShortSeg) {
-        const unsigned long long slot = atomicAdd(&st->long_count, 1ull);
-        long_list[slot] = (uint32_t)j;
-        return;
-    }
-    double sum = 0.0, comp = 0.0;
-    if (o.compensated) {
-        for (uint32_t i = s0; i < s1; ++i) {
-            double s, e;
-            two_sum(sum, vals[i], s, e);
-            sum = s;
-            comp += e;
-        }
-        sum += comp;
-    } else {
-        for (uint32_t i = s0; i < s1; ++i) sum += vals[i];
-    }
-    o.vals[o.dense ? (int64_t)key : j] = sum;
-}
-
-__global__ void __launch_bounds__(256) k_long_seg(const uint64_t* __restrict__ keys, const double* __restrict__ vals,
-                                                  const uint32_t* __restrict__ seg_start,
-                                                  const uint32_t* __restrict__ long_list, SegOut o, Status* st) {
-    const unsigned long long L = *(volatile unsigned long long*)&st->long_count;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w = warp; (unsigned long long)w < L; w += nwarps) {
-        const uint32_t j = long_list[w];
-        const uint32_t s0 = seg_start[j], s1 = seg_start[j + 1];
-        double sum = 0.0, comp = 0.0;
-        for (uint32_t i = s0 + lane; i < s1; i += 32) {
-            if (o.compensated) {
-                double s, e;
-                two_sum(sum, vals[i], s, e);
-                sum = s;
-                comp += e;
-            } else {
-                sum += vals[i];
-            }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const double os = __shfl_xor_sync(0xffffffffu, sum, off);
-            const double oc = __shfl_xor_sync(0xffffffffu, comp, off);
-            if (o.compensated) {
-                // combine (sum, comp) pairs in a fixed order: lower lane first
-                const bool lower = (lane & off) == 0;
-                const double a = lower ? sum : os, b = lower ? os : sum;
-                double s, e;
-                two_sum(a, b, s, e);
-                comp = (lower ? comp + oc : oc + comp) + e;
-                sum = s;
-            } else {
-                const bool lower = (lane & off) == 0;
-                sum = lower ? sum + os : os + sum;
-            }
-        }
-        if (lane == 0) {
-            const double r = o.compensated ? sum + comp : sum;
-            o.vals[o.dense ? (int64_t)keys[s0] : (int64_t)j] = r;
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1191,7 +1018,8 @@ static void rbk_launch(const H& hd, const Src& src, int64_t n, void* state, cons
 
 void launch_reduce_by_key(const uint64_t* keys, const double* vals, int64_t n, void* state, const StreamDesc& p,
                           const SegOut& o, Status* st, cudaStream_t stream) {
-    rbk_launch<false>(KeyHeads{keys}, PairTerms{vals}, n, state, p, o, st, stream);
+    if (o.compensated) rbk_launch<true>(KeyHeads{keys}, PairTerms{vals}, n, state, p, o, st, stream);
+    else rbk_launch<false>(KeyHeads{keys}, PairTerms{vals}, n, state, p, o, st, stream);
 }
 
 // The key of every run of a sorted key array, by run index (vals: any n
@@ -1212,19 +1040,5 @@ void launch_reduce_by_key_prepared(const uint8_t* head_bits, const uint64_t* row
     else rbk_launch<false>(BitHeads{head_bits, row_keys}, PrepTermsDev{terms}, n, state, p, o, st, stream);
 }
 
-void launch_seg_reduce(const uint64_t* keys, const double* vals, int64_t n, uint32_t* seg_start,
-                       unsigned long long* lookback, uint32_t* ticket, uint32_t* long_list, const StreamDesc& p,
-                       const SegOut& o, Status* st, cudaStream_t stream) {
-    if (n <= 0) return;
-    const int64_t ntiles = (n + kSegTile - 1) / kSegTile;
-    cudaMemsetAsync(lookback, 0, (size_t)ntiles * sizeof(unsigned long long), stream);
-    cudaMemsetAsync(ticket, 0, sizeof(uint32_t), stream);
-    TTV_LAUNCH("seg_heads", stream, k_seg_heads<<<(unsigned)ntiles, kSegThreads, 0, stream>>>(keys, n, seg_start, lookback, ticket, st));
-    TTV_LAUNCH("seg_sum", stream, k_seg_sum<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(keys, vals, seg_start, p, o, long_list, st));
-    int dev = 0, nsm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    TTV_LAUNCH("long_seg", stream, k_long_seg<<<(unsigned)(nsm * 4), 256, 0, stream>>>(keys, vals, seg_start, long_list, o, st));
-}
 
 }  // namespace ttv
