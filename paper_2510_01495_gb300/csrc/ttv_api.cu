@@ -8,9 +8,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ttv_internal.cuh"
 
 namespace ttv {
+
+// An NVTX range around one public call, so that a timeline (nsys, or ncu's
+// NVTX filters) shows which TTV, batch, preparation or run each kernel
+// belongs to; without an attached tool a push/pop costs a few nanoseconds.
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope&) = delete;
+    NvtxScope& operator=(const NvtxScope&) = delete;
+};
+
 // kernels in ttv_stream.cu / ttv_sort.cu
 void launch_keys_terms(const StreamDesc& p, uint64_t* keys, double* terms, cudaStream_t stream);
 bool keys_terms_vec_applicable(const StreamDesc& p, int npass);
@@ -775,6 +788,7 @@ const char* ttv_last_error(void) { return g_err.c_str(); }
 int ttv_multi_checked(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const void* const* vecs,
                       const int64_t* vec_lens, ttv_dtype v_dtype, ttv_out* out, const ttv_opts* opts,
                       ttv_stream_t stream) {
+    NvtxScope nvtx_range("ttv_multi");
     g_err.clear();
     if (!out) return fail(TTV_ERR_ARG, "null result");
     ttv_opts def;
@@ -871,6 +885,7 @@ void ttv_out_free(ttv_out* out) {
 
 int ttv_autotune(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const void* const* vecs, ttv_dtype v_dtype,
                  const ttv_opts* opts, int32_t trials, ttv_tune_result* res, ttv_stream_t stream_) {
+    NvtxScope nvtx_range("ttv_autotune");
     g_err.clear();
     if (!res) return fail(TTV_ERR_ARG, "null tuning result");
     memset(res, 0, sizeof *res);
@@ -1067,6 +1082,7 @@ int ttv_tune_count(void) {
 // ---- prepared tensors ------------------------------------------------------
 
 int ttv_prepare(const ttv_tensor* t, const int32_t* modes, int32_t n_v, ttv_prepared** out, ttv_stream_t stream_) {
+    NvtxScope nvtx_range("ttv_prepare");
     g_err.clear();
     if (!out) return fail(TTV_ERR_ARG, "null result handle");
     *out = nullptr;
@@ -1232,6 +1248,7 @@ int ttv_prepare(const ttv_tensor* t, const int32_t* modes, int32_t n_v, ttv_prep
 
 int ttv_prepared_run(const ttv_prepared* h, const void* const* vecs, const int64_t* vec_lens, ttv_dtype v_dtype,
                      ttv_out* out, const ttv_opts* opts, ttv_stream_t stream) {
+    NvtxScope nvtx_range("ttv_prepared_run");
     g_err.clear();
     if (!h || !vecs || !out) return fail(TTV_ERR_ARG, "null prepared tensor, vectors or result");
     if (v_dtype != TTV_F64 && v_dtype != TTV_F32) return fail(TTV_ERR_ARG, "bad vector dtype");
@@ -1263,6 +1280,7 @@ int ttv_mttkrp_workspace_size(const ttv_prepared* h, int32_t rank, size_t* bytes
 
 int ttv_mttkrp_prepared(const ttv_prepared* h, const double* const* factors, int32_t rank, double* out,
                         void* workspace, size_t workspace_bytes, ttv_stream_t stream_) {
+    NvtxScope nvtx_range("ttv_mttkrp");
     g_err.clear();
     if (!h || !factors || !out) return fail(TTV_ERR_ARG, "null prepared tensor, factors or result");
     if (rank < 1 || rank > TTV_MTTKRP_MAX_RANK) return fail(TTV_ERR_ARG, "rank %d outside 1..%d", rank, TTV_MTTKRP_MAX_RANK);
@@ -1330,6 +1348,7 @@ int ttv_dot_workspace_size(int64_t n, size_t* bytes) {
 
 int ttv_dot(const void* x, const void* y, int64_t n, ttv_dtype dtype, double* out, void* workspace,
             size_t workspace_bytes, ttv_stream_t stream_) {
+    NvtxScope nvtx_range("ttv_dot");
     g_err.clear();
     if (n < 0 || !out || (n > 0 && (!x || !y))) return fail(TTV_ERR_ARG, "null operand or negative length");
     if (dtype != TTV_F64 && dtype != TTV_F32) return fail(TTV_ERR_ARG, "bad dtype");
@@ -1360,6 +1379,7 @@ int ttv_matvec_workspace_size(int64_t n1, int64_t n2, int64_t stride_row, int64_
 
 int ttv_matvec(const void* A, int64_t n1, int64_t n2, int64_t stride_row, int64_t stride_col, ttv_dtype dtype,
                const void* x, double* y, void* workspace, size_t workspace_bytes, ttv_stream_t stream_) {
+    NvtxScope nvtx_range("ttv_matvec");
     g_err.clear();
     if (n1 < 0 || n2 < 0) return fail(TTV_ERR_ARG, "negative size");
     if ((n1 > 0 && !y) || (n1 > 0 && n2 > 0 && (!A || !x))) return fail(TTV_ERR_ARG, "null operand");
@@ -1620,6 +1640,7 @@ void ttv_batch_release(void) {
 }
 
 int ttv_batch(const ttv_problem* probs, int32_t n, ttv_out* outs, const ttv_opts* opts, ttv_stream_t stream_) {
+    NvtxScope nvtx_range("ttv_batch");
     g_err.clear();
     if (!probs || !outs || n < 0) return fail(TTV_ERR_ARG, "bad batch arguments");
     if (n == 0) return TTV_OK;
