@@ -13,12 +13,12 @@
 // in row_keys.  The nonzeros are cut into chunks of 128.  A group of lanes
 // per chunk walks its nonzeros in order (lanes own rank components; a
 // nonzero per lane is loaded at a time and broadcast with shuffles), writes
-// every row that starts
-// and ends inside the chunk, and leaves the sums of the chunk's first (open
-// on the left) and last (open on the right) pieces in a side buffer.  A
-// second pass adds, for every row that crosses chunk ends, its pieces in
-// chunk order.  Every sum is thus formed in one fixed order: results are
-// bit-identical from run to run.
+// every row that starts and ends inside the chunk, and leaves the sums of
+// the chunk's first (open on the left) and last (open on the right) pieces
+// in a side buffer.  A fix-up pass adds, for every row that crosses chunk
+// ends, its pieces in chunk order, taking whole aligned runs of 64 and 4096
+// chunks from precomputed sums.  Every sum is thus formed in an order fixed
+// by the layout: results are bit-identical from run to run.
 #include <algorithm>
 
 #include "ttv_internal.cuh"
