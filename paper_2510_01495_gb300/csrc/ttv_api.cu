@@ -453,8 +453,9 @@ static Status* direct_status(OutState* st, cudaStream_t stream) {
 
 // pyttb's conversion (Sec. 3.3): a sparse result with more than half of its
 // cells present becomes a dense array.  Library-owned results move to a new
-// dense buffer; a caller's value buffer is reused when it holds every cell,
-// else the result stays sparse.
+// dense buffer; a caller's value buffer is reused when it holds every cell.
+// When neither is possible (no room for the dense array or its scratch) the
+// result stays sparse, as it was computed.
 static int auto_to_dense(ttv_out* out, OutState* s) {
     const int64_t n = out->nnz, nk = (int64_t)s->nkeys;
     cudaStream_t stream = s->stream;
@@ -462,7 +463,10 @@ static int auto_to_dense(ttv_out* out, OutState* s) {
     if (s->owned_vals) {
         double* dense = nullptr;
         e = cudaMallocAsync((void**)&dense, (size_t)nk * sizeof(double), stream);
-        if (e != cudaSuccess) return cuda_fail(e, "dense result allocation");
+        if (e != cudaSuccess) {       // no room for the dense form: the sparse result stands
+            cudaGetLastError();
+            return TTV_OK;
+        }
         launch_coo_to_dense(out->subs, static_cast<const double*>(out->vals), n, out->order, out->shape, dense,
                             nk, stream);
         cudaFreeAsync(s->owned_vals, stream);
@@ -472,7 +476,10 @@ static int auto_to_dense(ttv_out* out, OutState* s) {
     } else if (out->vals_capacity >= nk) {
         double* tmp = nullptr;
         e = cudaMallocAsync((void**)&tmp, (size_t)std::max<int64_t>(n, 1) * sizeof(double), stream);
-        if (e != cudaSuccess) return cuda_fail(e, "dense conversion scratch");
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return TTV_OK;
+        }
         cudaMemcpyAsync(tmp, out->vals, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, stream);
         launch_coo_to_dense(out->subs, tmp, n, out->order, out->shape, static_cast<double*>(out->vals), nk, stream);
         cudaFreeAsync(tmp, stream);
