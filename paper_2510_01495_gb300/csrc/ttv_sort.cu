@@ -877,8 +877,14 @@ struct RbkEmitSmem {
     RbkScanSmem ss;
 };
 
+// Resident CTAs per SM: 5 for prepared runs (48 registers; measured 1.26 ms
+// against 1.34 at 4 on the 1e8 Zipf run), 4 for sorted pairs (their key
+// comparisons spill too much at 48 registers: 1.05 against 1.04 ms).
+template <class H>
+constexpr int rbk_emit_ctas() { return H::kBits ? 5 : 4; }
+
 template <bool kComp, class H, class Src>
-__global__ void __launch_bounds__(kRbkThreads, 4) k_rbk_emit(H hd, Src src, int64_t n,
+__global__ void __launch_bounds__(kRbkThreads, rbk_emit_ctas<H>()) k_rbk_emit(H hd, Src src, int64_t n,
                                                              const RbkSum* __restrict__ ingroup,
                                                              const RbkSum* __restrict__ gprefix,
                                                              const unsigned long long* __restrict__ gheads,
