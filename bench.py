@@ -50,6 +50,9 @@ WORKLOADS = {
         desc="dense dot product (Eq. 1) of two float64 vectors of 1e8 elements, U[0,1)"),
     "matvec_1e4": dict(make=None, fmt=None,
         desc="dense matrix-vector product (Eq. 2), float64 10000x10000 matrix (--order C or F), U[0,1)"),
+    "paper_sweep": dict(make=None, fmt=None,
+        desc="the paper's TTV experiment (Sec. 4.3): n^3 COO tensors, n = 100..1200, density 1 %, values and "
+             "vector U[0,1], vector along the second mode; one line with every n"),
     "single_3way_100": dict(
         make=lambda dev, seed, nnz=None: S.single_3way_100(seed=seed, device=dev), fmt="sparse",
         desc="single TTV mode 0 of a 100^3 COO tensor, nnz 1e4 uniform distinct, sparse 100x100 result"),
@@ -374,7 +377,7 @@ def main():
     args = ap.parse_args()
     if args.seed == 0:
         args.seed = {"allbutone_4way_1000": 2, "single_5way_zipf": 3, "single_3way_100": 1, "batch_512": 5,
-                     "serve_64": 6, "dot_1e8": 8, "matvec_1e4": 9}[args.workload]
+                     "serve_64": 6, "dot_1e8": 8, "matvec_1e4": 9, "paper_sweep": 4}[args.workload]
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -389,6 +392,8 @@ def main():
         return run_mttkrp(args, rank, world, local_rank)
     if args.workload in ("dot_1e8", "matvec_1e4"):
         return run_dense(args, rank, world, local_rank)
+    if args.workload == "paper_sweep":
+        return run_paper_sweep(args, rank, world, local_rank)
 
     import paper_2510_01495_gb300 as ttv
     torch.cuda.set_device(local_rank)
@@ -1086,6 +1091,63 @@ def run_dense(args, rank, world, local_rank):
             sample = f"first {rows} of 10000 rows ({args.order} order), one call, {dt:.2f} s"
         line["cpu_baseline"] = {"value": m / dt / 1e9, "unit": "Gelem/s", "cores": 1, "kind": "oracle",
                                 "sample": sample}
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_paper_sweep(args, rank, world, local_rank):
+    """The paper's own TTV experiment on the GPU: for n = 100..1200 one TTV of
+    an n^3 tensor with 0.01 n^3 distinct nonzeros along the second mode
+    (sparse n x n result), timed with CUDA events over --steps calls of the C
+    ABI after --warmup; the line's value is the n = 1200 rate."""
+    import paper_2510_01495_gb300 as ttv
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = init_ranks(world, dev)
+    ttv.load()
+    steps = min(args.steps, 200)
+    rows = []
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    for n in range(100, 1300, 100):
+        p = S.paper_sweep(n, seed=replica_seed(args.seed, rank), device=dev)
+        t = p.tensor
+        subs = t.subs.t().contiguous().t()
+        ws = torch.empty(max(1, ttv.workspace_size(subs, t.vals, t.shape, p.modes)), dtype=torch.uint8, device=dev)
+        nrow, nval = ttv.out_capacity(subs, t.vals, t.shape, p.modes)
+        ov = torch.empty(nval, dtype=torch.float64, device=dev)
+        osb = torch.empty((max(1, nrow), 2), dtype=torch.int64, device=dev)
+
+        def call():
+            return ttv.ttv_multi(subs, t.vals, t.shape, p.modes, p.vecs, workspace=ws, out_vals=ov, out_subs=osb)
+        for _ in range(args.warmup):
+            call()
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(steps):
+            r = call()
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        ms = max_over_ranks(dist, ev0.elapsed_time(ev1) / steps, dev)
+        rows.append({"n": n, "nnz": t.nnz, "nnz_out": int(r.vals.numel()), "ms": ms,
+                     "gnnz_s": t.nnz * world / (ms * 1e-3) / 1e9})
+        del p, t, subs, ws, ov, osb
+    clk = clocks.stop()
+    last = rows[-1]
+    line = {
+        "metric": "TTV nonzeros/sec", "value": last["gnnz_s"], "unit": "GNNZ/s", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": last["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "paper_sweep", "desc": WORKLOADS["paper_sweep"]["desc"],
+                   "timing": "CUDA events around --steps synchronous ttv_multi calls (result size read each call)",
+                   "l2": "inputs up to 553 MB; the small sizes are L2-resident"},
+        "sweep": rows, "clocks": clk,
+    }
     if dist:
         dist.destroy_process_group()
     if rank == 0:
