@@ -369,7 +369,30 @@ def check_mttkrp_bruteforce_rounded(mttkrp, ttv=None):
                 assert abs(Fraction(float(M[i, r])) - ref[i][r]) <= Fraction(bound) * (1 + 1e-12), (seed, i, r)
 
 
-MTTKRP_CHECKS = [check_mttkrp_equals_ttv_columns, check_mttkrp_bruteforce_exact, check_mttkrp_bruteforce_rounded]
+def check_mttkrp_linear_in_each_factor(mttkrp, ttv=None):
+    """M is linear in every factor matrix: with dyadic entries small enough
+    that every product and sum is exact, M(.., A_m + B_m, ..) equals
+    M(.., A_m, ..) + M(.., B_m, ..) bit for bit, and scaling A_m by 2 scales M
+    by 2."""
+    for seed in range(20):
+        d = 2 + seed % 3
+        subs, vals, shape, facs, mode = mttkrp_case(seed + 900, d, rank=3, dyadic=True)
+        m = (mode + 1 + seed % (d - 1)) % d
+        g = rng(9100 + seed)
+        other = g.integers(-8, 9, size=facs[m].shape).astype(np.float64) / 8.0
+        base = mttkrp(subs, vals, shape, mode, facs)
+        alt = list(facs)
+        alt[m] = other
+        plus = list(facs)
+        plus[m] = facs[m] + other
+        twice = list(facs)
+        twice[m] = 2.0 * facs[m]
+        assert np.array_equal(mttkrp(subs, vals, shape, mode, plus), base + mttkrp(subs, vals, shape, mode, alt)), seed
+        assert np.array_equal(mttkrp(subs, vals, shape, mode, twice), 2.0 * base), seed
+
+
+MTTKRP_CHECKS = [check_mttkrp_equals_ttv_columns, check_mttkrp_bruteforce_exact, check_mttkrp_bruteforce_rounded,
+                 check_mttkrp_linear_in_each_factor]
 
 
 # ---- dense dot product (Eq. 1) and matrix-vector product (Eq. 2) --------------------

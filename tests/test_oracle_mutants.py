@@ -43,6 +43,8 @@ MTTKRP_MUTANTS = {
                                 "if (m != mode) t = t * factors[m][(subs[k * d + m] % shape[m]) * rank + 0];"),
     "mttkrp_wrong_output_row": ("const int64_t i = subs[k * d + mode];",
                                 "const int64_t i = subs[k * d + mode] == 0 ? 0 : subs[k * d + mode] - 1;"),
+    "mttkrp_factor_read_column_major": ("if (m != mode) t = t * factors[m][subs[k * d + m] * rank + r];",
+                                        "if (m != mode) t = t * factors[m][r * shape[m] + subs[k * d + m]];"),
     "mttkrp_no_compensation": ("if (fabs(*sum) >= fabs(t)) *c += (*sum - s) + t;\n            else                       *c += (t - s) + *sum;",
                                ""),
 }
