@@ -277,9 +277,11 @@ int ttv_tune_lookup(const ttv_tensor *t, const int32_t *modes, int32_t n_v, cons
  * with fresh vectors.  The grouping of Sec. 3.3 (one result row per distinct
  * surviving tuple, ascending) depends on the tensor only, so ttv_prepare
  * sorts the nonzeros once by their surviving key (stable: equal keys keep
- * input order) and keeps, in that order, the keys (8 bytes per nonzero), the
- * values (val_dtype) and the subscripts of the modes in S (int32; every mode
- * in S must be smaller than 2^31).  ttv_prepared_run is then one streaming
+ * input order) and keeps, in that order, the values (val_dtype) and the
+ * subscripts of the modes in S (int32; every mode in S must be smaller than
+ * 2^31), plus a bitmap of where each result row starts (1 bit per nonzero)
+ * and the key of every result row; with one surviving mode it also indexes
+ * the rows per 128-nonzero chunk for MTTKRP.  ttv_prepared_run is then one streaming
  * reduce-by-key over those arrays with the terms vals * prod x_m[sub_m]
  * formed on the fly in increasing mode order: its result equals, bit for bit,
  * that of ttv_multi with path SORT and fp64 accumulation on the same inputs.
