@@ -35,3 +35,15 @@ def test_exclude_dims_is_the_complement():
 def test_invalid_specifications(args):
     with pytest.raises(ValueError):
         ttv.resolve_dims(args.pop("d"), args.pop("nvec"), **args)
+
+
+def test_sptensor_arrays_of_sparse_and_dense_results():
+    import torch
+    subs = torch.tensor([[0, 1], [2, 0]], dtype=torch.int64)
+    vals = torch.tensor([1.5, -2.0], dtype=torch.float64)
+    s, v, shp = ttv.Result(subs, vals, (3, 2), False).to_sptensor_arrays()
+    assert s.tolist() == [[0, 1], [2, 0]] and v.tolist() == [[1.5], [-2.0]] and shp == (3, 2)
+    dense = torch.tensor([[0.0, 1.5], [0.0, 0.0], [-2.0, 0.0]], dtype=torch.float64)
+    s, v, shp = ttv.Result(None, dense, (3, 2), True).to_sptensor_arrays()
+    # the nonzero cells, in row-major (pyttb unique) order, values as a column
+    assert s.tolist() == [[0, 1], [2, 0]] and v.tolist() == [[1.5], [-2.0]] and shp == (3, 2)
