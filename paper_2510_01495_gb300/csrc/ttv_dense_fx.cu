@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_dense_fx(FxParams f) {
             tv[u].E = -(1 << 28);
             tv[u].neg = 0;
             tv[u].bad = 0;
+            tv[u].wide = 0;
             key[u] = 0xFFFFFFFFu;
             if (j >= cnt) continue;
             const int64_t k = k0 + j;
@@ -171,17 +172,29 @@ __global__ void __launch_bounds__(kFxThreads, 1) k_dense_fx(FxParams f) {
             Sig t = decompose(val);
             uint64_t kk = 0;
             bool good = true;
+            int64_t ss[kMaxD];
 #pragma unroll
             for (int m = 0; m < kMaxD; ++m) {
+                ss[m] = 0;
                 if (m >= d) break;
                 int64_t sm;
                 if (f.aos) sm = (j * d + m < aos_copied) ? scol[j * d + m] : p.subs[k * d + m];
                 else sm = j < cs ? scol[(size_t)m * f.tile + j] : p.subs[(int64_t)m * p.smode + k];
                 if (sm < 0 || sm >= p.shape[m]) { good = false; continue; }
+                ss[m] = sm;
                 if ((p.smask >> m) & 1u) sig_mul(t, decompose(load_vec(p, sv, m, sm)));
                 else kk += (uint64_t)sm * p.kstride[m];
             }
             if (!good) { set_error(p.status, kErrSubscript); continue; }
+            if (t.wide && !t.bad) {
+                // a partial product left the normal range: the term is Eq. 3's
+                // binary64 chain itself, taken exactly into the fixed point
+                double tt = val;
+#pragma unroll
+                for (int m = 0; m < kMaxD; ++m)
+                    if (m < d && ((p.smask >> m) & 1u)) tt = tt * load_vec(p, sv, m, ss[m]);
+                t = decompose(tt);
+            }
             if (t.bad) set_error(p.status, kErrNonFinite);
             tv[u] = t;
             key[u] = (uint32_t)kk;

@@ -41,7 +41,7 @@ __device__ __forceinline__ void dense_item(const StreamDesc& p, const double* sv
             if ((p.smask >> m) & 1u) sig_mul(a, sig_of(sve[p.voff[m] + s[m]]));
             else key += (uint64_t)s[m] * p.kstride[m];
         }
-        if (a.bad) {
+        if (a.bad | a.wide) {
             double tt = val;
 #pragma unroll
             for (int m = 0; m < D; ++m)

@@ -75,11 +75,13 @@ struct Sig {
     int E;
     uint32_t neg;
     uint32_t bad;     // inf or nan
+    uint32_t wide;    // some nonzero partial product left [2^-1021, 2^1023)
 };
 
 __device__ __forceinline__ Sig decompose(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     Sig s;
+    s.wide = 0;
     s.neg = (uint32_t)(b >> 63);
     const int ex = (int)((b >> 52) & 0x7FF);
     const unsigned long long f = b & ((1ull << 52) - 1);
@@ -101,7 +103,11 @@ __device__ __forceinline__ Sig decompose(double x) {
 }
 
 // a *= b on significands: high 64 bits of the 128-bit product, renormalised
-// (truncation error below 2^-62 relative).
+// (truncation error below 2^-62 relative). A nonzero partial product whose
+// exponent falls outside [-1021, 1022] sets `wide`: there the binary64 chain
+// of Eq. 3 may overflow, underflow or lose bits to a subnormal step, so the
+// caller recomputes that term as the chain itself. The one-exponent margin
+// covers the chain's own rounding of the partial products.
 __device__ __forceinline__ void sig_mul(Sig& a, const Sig& b) {
     const unsigned long long hi = __umul64hi(a.M, b.M);
     const bool top = (hi >> 63) != 0;
@@ -110,6 +116,7 @@ __device__ __forceinline__ void sig_mul(Sig& a, const Sig& b) {
     a.neg ^= b.neg;
     a.bad |= b.bad;
     if (b.M == 0) a.M = 0;
+    a.wide |= (uint32_t)(a.M != 0) & (uint32_t)((unsigned)(a.E + 1021) > 2043u);
 }
 
 // Nearest binary64 of a significand (ties to even); infinities and
@@ -139,6 +146,7 @@ struct __align__(16) SigEntry {
 
 __device__ __forceinline__ Sig sig_of(const SigEntry& e) {
     Sig s;
+    s.wide = 0;
     s.M = e.M;
     s.E = e.E;
     s.neg = e.neg_bad & 1u;
@@ -238,7 +246,9 @@ __device__ __forceinline__ bool key_term(const StreamDesc& p, const double* sv, 
 // Same as key_term with the product formed on integer units: the value and
 // each gathered entry as significands, multiplied exactly to 64 bits and
 // rounded once to binary64 (within one unit of the binary64 product chain).
-// Inf/nan operands take the binary64 chain so they propagate as usual.
+// Inf/nan operands, and terms whose partial products leave the normal
+// binary64 range, take the binary64 chain, so overflow, underflow and
+// subnormal steps round exactly as Eq. 3's chain does.
 __device__ __forceinline__ bool key_term_sig(const StreamDesc& p, const SigEntry* sve, const int64_t* s, double val,
                                              uint64_t& key, double& t) {
     bool good = true;
@@ -262,7 +272,7 @@ __device__ __forceinline__ bool key_term_sig(const StreamDesc& p, const SigEntry
         }
     }
     key = kk;
-    if (good && acc.bad) {
+    if (good && (acc.bad | acc.wide)) {
         double tt = val;
 #pragma unroll
         for (int m = 0; m < kMaxD; ++m)

@@ -325,6 +325,11 @@ __device__ __forceinline__ void nm_add(double& s, double& c, double x) {
     s = t;
 }
 
+// The value of a compensated sum s + c.  Once s is not finite the plain sum
+// is the value: the correction would turn a lone infinity into a NaN, while
+// Eq. 3's plain sum keeps it.
+__device__ __forceinline__ double nm_value(double s, double c) { return isfinite(s) ? s + c : s; }
+
 // (ca, fa, va, ka) . (cb, fb, vb, kb) -> b; kComp carries the error terms k
 template <bool kComp>
 __device__ __forceinline__ void seg_combine(uint32_t ca, uint32_t fa, double va, double ka, uint32_t& cb,
@@ -514,7 +519,7 @@ __device__ __forceinline__ void rbk_load(const H& hd, const Src& src, int64_t n,
             if (i < r.nmine) {
                 if ((r.heads >> i) & 1u) {
                     if constexpr (kComp) {
-                        r.done[i] = acc + ak;       // a run closed inside the range: final value
+                        r.done[i] = nm_value(acc, ak);   // a run closed inside the range: final value
                         if (i == fh) { r.first_done = acc; r.first_k = ak; }
                         ak = 0.0;
                     } else {
@@ -561,7 +566,7 @@ __device__ __forceinline__ void rbk_load(const H& hd, const Src& src, int64_t n,
             if (r.k[i] != prev || r.g0 + i == 0) {
                 if constexpr (kComp) {
                     if (!r.flag) { r.first_done = acc; r.first_k = ak; }
-                    r.done[i] = acc + ak;
+                    r.done[i] = nm_value(acc, ak);
                     ak = 0.0;
                 } else {
                     if (!r.flag) r.first_done = acc;
@@ -919,7 +924,7 @@ __global__ void __launch_bounds__(kRbkThreads, rbk_emit_ctas<H>()) k_rbk_emit(H 
     const int fh = r.heads ? __ffs(r.heads) - 1 : kRbkItems;
     double closed_first = r.first_done, closed_first_k = kComp ? r.first_k : 0.0;
     cat_sum<kComp>(base, base_k, closed_first, closed_first_k);
-    if (kComp) closed_first = closed_first + closed_first_k;
+    if (kComp) closed_first = nm_value(closed_first, closed_first_k);
 #pragma unroll
     for (int i = 0; i < kRbkItems; ++i) {
         if (i < r.nmine) {
@@ -938,7 +943,7 @@ __global__ void __launch_bounds__(kRbkThreads, rbk_emit_ctas<H>()) k_rbk_emit(H 
         if constexpr (!H::kBits) sm.row_key[h - first] = prev;
         double lv = r.open, lk = kComp ? r.open_k : 0.0;
         if (!r.flag) cat_sum<kComp>(base, base_k, lv, lk);
-        sm.row_val[h - first] = kComp ? lv + lk : lv;
+        sm.row_val[h - first] = kComp ? nm_value(lv, lk) : lv;
     }
     __syncthreads();
     const int nrows = (int)tc - first + (last_tile ? 1 : 0);

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_dense_reduce(int64_t P, int G, const do
     }
     any = __any_sync(0xffffffffu, any) ? 1u : 0u;
     if (lane == 0) {
-        cell_vals[cell] = compensated ? sum + comp : sum;
+        cell_vals[cell] = (compensated && isfinite(sum)) ? sum + comp : sum;   // an infinite sum stays infinite
         if (want_presence) cell_flags[cell] = any;
     }
 }

@@ -209,6 +209,33 @@ def vector(seed: int, stream: int, n: int, kind="u11", device="cpu") -> torch.Te
     raise ValueError(kind)
 
 
+# Exponent offsets for wide-range inputs: most entries keep their scale, the
+# rest move by powers of two chosen so that chained products of three factors
+# overflow, underflow to zero, or land among the subnormals.
+WIDE_EXPONENTS = (0, 0, 0, 0, 0, 0, 300, -300, 600, -600, 350, -350, -700)
+
+
+def wide_exponents(seed: int, stream: int, n: int, device="cpu") -> torch.Tensor:
+    """n seeded exponent offsets drawn from WIDE_EXPONENTS (int64)."""
+    idx = uniform_int(seed, stream, n, len(WIDE_EXPONENTS), device=device)
+    return torch.tensor(WIDE_EXPONENTS, dtype=torch.int64, device=device)[idx]
+
+
+def widen(problem: "Problem", seed: int) -> "Problem":
+    """The same problem with values and vector entries multiplied by 2^e,
+    e drawn per entry from WIDE_EXPONENTS (exact: only the exponent moves,
+    while it stays in the binary64 range)."""
+    t = problem.tensor
+    ev = wide_exponents(seed, 7001, t.nnz, device=t.vals.device)
+    vals = torch.ldexp(t.vals.to(torch.float64), ev.to(torch.float64))
+    vecs = []
+    for j, v in enumerate(problem.vecs):
+        e = wide_exponents(seed, 7100 + j, v.shape[0], device=v.device)
+        vecs.append(torch.ldexp(v.to(torch.float64), e.to(torch.float64)))
+    return Problem(SparseTensor(t.subs, vals, t.shape), list(problem.modes), vecs, dense=problem.dense,
+                   name=problem.name + "_wide", meta=dict(problem.meta))
+
+
 # ----------------------------------------------------------------------------
 # Workloads.  Sizes follow the TTV configurations the library is measured on
 # and the paper's own sweep (Sec. 4.3: 3-way, n in {100..1200}, density 1 %,

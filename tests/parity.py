@@ -5,7 +5,8 @@ Tolerance (FP64): |x - ref| <= RTOL * max(|ref|, FLOOR * A) per output
 entry, A = sum of |terms| in that entry's group (the oracle's TTV of |vals|
 with |vectors|).  RTOL = 1e-12 relative; the floor only matters where the
 group cancels to (near) zero, where a relative bound is not attainable by
-any summation order.  Subscripts and counts must match bit for bit.
+any summation order.  Subscripts and counts must match bit for bit, and a
+non-finite result must be the oracle's: the same infinity, or nan for nan.
 """
 from __future__ import annotations
 
@@ -32,9 +33,18 @@ def assert_close(x, ref, A, rtol=RTOL, floor=FLOOR, what=""):
     ref = np.asarray(ref, dtype=np.float64).reshape(-1)
     A = np.asarray(A, dtype=np.float64).reshape(-1)
     assert x.shape == ref.shape, (what, x.shape, ref.shape)
-    err = np.abs(x - ref)
-    tol = rtol * np.maximum(np.abs(ref), floor * A)
-    bad = np.nonzero(err > tol)[0]
+    # non-finite results must match in kind: nan for nan, the same infinity
+    fin = np.isfinite(ref)
+    nf = np.nonzero(~fin | ~np.isfinite(x))[0]
+    if nf.size:
+        same = (np.isnan(x[nf]) & np.isnan(ref[nf])) | (x[nf] == ref[nf])
+        if not np.all(same):
+            i = nf[np.nonzero(~same)[0][0]]
+            raise AssertionError(f"{what}: non-finite mismatch at {i}: got {x[i]!r} want {ref[i]!r}")
+    with np.errstate(invalid="ignore"):
+        err = np.where(fin, np.abs(x - ref), 0.0)
+        tol = rtol * np.maximum(np.abs(ref), floor * np.where(np.isfinite(A), A, 0.0))
+    bad = np.nonzero(fin & (err > tol))[0]
     if bad.size:
         i = bad[0]
         raise AssertionError(f"{what}: {bad.size} values out of tolerance; first at {i}: "

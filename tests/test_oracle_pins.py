@@ -66,6 +66,39 @@ def test_nonfinite_terms_follow_ieee_sum():
     assert v[0] == inf and np.isnan(v[1]) and np.isnan(v[2]) and v[3] == -inf
 
 
+def test_product_chain_rounds_each_step():
+    """Eq. 3 forms vals[k] * x_m[.] one factor at a time in increasing mode
+    order, each step rounded to binary64.  Closed forms where that chain and
+    the exact product part: a partial product above the largest double stays
+    infinite, one below the smallest subnormal stays zero, and a product in
+    the subnormal range keeps only the bits that range holds."""
+    big, small = 2.0 ** 600, 2.0 ** -600
+    subs = np.zeros((1, 3), dtype=np.int64)
+    # val * x0 overflows before x1 brings it back
+    _, v, _ = oracle.ttv(subs, np.array([big]), (1, 1, 1), [0, 1], [np.array([big]), np.array([small])])
+    assert v[0] == float("inf")
+    # the same factors given in the other mode order: the chain order is fixed by the modes, not the list
+    _, v, _ = oracle.ttv(subs, np.array([big]), (1, 1, 1), [1, 0], [np.array([small]), np.array([big])])
+    assert v[0] == float("inf")
+    # small factors first: underflow to zero, then scaled back up it stays zero
+    _, v, _ = oracle.ttv(subs, np.array([-small]), (1, 1, 1), [0, 1], [np.array([small]), np.array([big])])
+    assert v[0] == 0.0
+    # big factor first: no partial leaves the range, the result is exact
+    _, v, _ = oracle.ttv(subs, np.array([small]), (1, 1, 1), [0, 1], [np.array([big]), np.array([small])])
+    assert v[0] == small
+    # subnormal result: 3 * 2^-1062 is representable exactly
+    _, v, _ = oracle.ttv(subs, np.array([0.75 * 2.0 ** -1000]), (1, 1, 1), [2], [np.array([2.0 ** -60])])
+    assert v[0] == 3 * 2.0 ** -1062
+    # subnormal result keeps 2^-1074 steps: (1 + 2^-52) * 2^-1060 rounds to 2^-1060
+    _, v, _ = oracle.ttv(subs, np.array([(1 + 2.0 ** -52) * 2.0 ** -1000]), (1, 1, 1), [2],
+                         [np.array([2.0 ** -60])])
+    assert v[0] == 2.0 ** -1060
+    # and a tie at the subnormal grid rounds to even: (1 + 2^-14) * 2^-1060 -> 2^-1060
+    _, v, _ = oracle.ttv(subs, np.array([(1 + 2.0 ** -15) * 2.0 ** -1000]), (1, 1, 1), [2],
+                         [np.array([2.0 ** -60])])
+    assert v[0] == 2.0 ** -1060
+
+
 @pytest.mark.parametrize("check", P.MTTKRP_CHECKS, ids=lambda c: c.__name__)
 def test_mttkrp_pin(check):
     check(oracle.mttkrp, oracle.ttv)

@@ -89,3 +89,24 @@ def test_workload_recipes():
         assert 3 <= d <= 5 and len(pr.modes) == 1 and 0 <= pr.modes[0] < d
         assert all(50 <= n <= 50_000 for n in pr.tensor.shape)
         assert pr.tensor.nnz <= 0.5 * float(np.prod([float(n) for n in pr.tensor.shape]))
+
+
+def test_widened_inputs_reach_every_edge_of_the_range():
+    """widen() really produces the cases the wide-range parity tests need:
+    chains of three factors that overflow part-way while the whole product is
+    finite, chains that underflow part-way while the product is not tiny, and
+    products in the subnormal range (exponents from frexp, no TTV arithmetic)."""
+    p = S.widen(S.Problem(S.sptenrand(21, (30, 20, 50, 40), 40_000, vals="u11"), [0, 1, 3],
+                          [S.vector(21, m, n) for m, n in ((0, 30), (1, 20), (3, 40))]), 21)
+    s = p.tensor.subs.numpy()
+    e = [np.frexp(p.tensor.vals.numpy())[1].astype(np.int64)]
+    for j, m in enumerate(p.modes):
+        e.append(np.frexp(p.vecs[j].numpy()[s[:, m]])[1].astype(np.int64))
+    part = np.cumsum(np.vstack(e), axis=0)[1:]     # frexp exponents of the partial products
+    total = part[-1]
+    assert np.any((part.max(axis=0) > 1030) & (total < 1000))
+    assert np.any((part.min(axis=0) < -1080) & (total > -1000))
+    assert np.any((total < -1030) & (total > -1070) & (part[:-1].min(axis=0) > -1020))
+    # scaling is exact: the significands are those of the unscaled inputs
+    base = S.sptenrand(21, (30, 20, 50, 40), 40_000, vals="u11").vals.numpy()
+    assert np.array_equal(np.frexp(p.tensor.vals.numpy())[0], np.frexp(base)[0])
