@@ -2,11 +2,15 @@
 """Benchmark of the GB300 sparse TTV library.
 
 One step = one complete TTV (stream, gather, scale, linearise, accumulate,
-emit) of the chosen workload through the library's C ABI.  Default workload:
-the all-but-one-mode TTV (vectors on modes 0, 1, 3) of a 1000^4 tensor with
-1e7 distinct uniform nonzeros, values and vectors U[-1,1], dense length-1000
-result; subscripts stored as d contiguous columns (pyttb's column-major
-layout).  Inputs (400 MB) are larger than L2, so no flush between steps.
+emit) of the chosen workload through the library's C ABI, computed from the
+raw COO input every step.  Default workload: the largest single TTV, mode 2
+of a 5-way 20000x5000x100000x2000x500 tensor with 1e8 distinct nonzeros whose
+subscripts are Zipf(1.2) per mode, values N(0,1), vector U[-1,1], sparse
+4-way result of about 6.1e7 rows; subscripts stored as d contiguous columns
+(pyttb's column-major layout).  Inputs (4.8 GB) are larger than L2, so no
+flush between steps.  The roofline of that workload is the whole step's:
+algorithmic bytes (subs + vals once, the vector once, the result rows once)
+over the step time.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -58,6 +62,9 @@ WORKLOADS = {
         desc="single TTV mode 0 of a 100^3 COO tensor, nnz 1e4 uniform distinct, sparse 100x100 result"),
 }
 
+# Nonzeros of the single-tensor workloads at full size.
+WORKLOAD_NNZ = {"allbutone_4way_1000": 10_000_000, "single_5way_zipf": 100_000_000, "single_3way_100": 10_000}
+
 # Kernel whose roofline is reported, per workload, and its algorithmic bytes
 # per launch: every nonzero's d subscripts and value read once, plus the
 # contracted vectors once.
@@ -83,9 +90,18 @@ def _prepared_emit_bytes(problem, ab):
 
 DOMINANT_PREPARED = [("rbk_emit", _prepared_emit_bytes)]
 
+# Workloads whose step runs several kernels of comparable weight: their
+# "roofline" is taken over the whole step (the algorithmic bytes of one TTV
+# over the step time); the dominant kernel's own figure is reported beside it.
+STEP_ROOFLINE = {"single_5way_zipf"}
+
 DOMINANT = {"allbutone_4way_1000": [("dense_accum", _stream_bytes), ("dense_fx", _stream_bytes)],
             "single_5way_zipf": [("onesweep", _pass_bytes), ("keys_terms", _stream_bytes)],
             "single_3way_100": [("dense_accum", _stream_bytes), ("dense_fx", _stream_bytes)]}
+
+# DRAM bytes of one whole step of the step-roofline workloads, from an ncu
+# capture (null until one is taken on the current sources).
+STEP_TRAFFIC = {}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel from an ncu capture of this workload (summary under profiles/), with
@@ -314,10 +330,14 @@ def run_reference(args, rank, world):
         print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm covers the single-tensor TTV "
                           f"workloads, not {args.workload}"}), flush=True)
         return
-    problem = wl["make"]("cpu", args.seed, args.nnz)
+    # The generator keeps the first distinct rows in draw order, so the first
+    # m nonzeros of a smaller draw are exactly the full workload's first m:
+    # only the largest sample a step can use is drawn.
+    problem = wl["make"]("cpu", args.seed, min(args.nnz or WORKLOAD_NNZ[args.workload], args.ref_sample))
     import oracle
     oracle.build()
     t = problem.tensor
+    full = args.nnz or WORKLOAD_NNZ[args.workload]
     subs, vals = t.subs.numpy(), t.vals.numpy()
     vecs = [v.numpy() for v in problem.vecs]
     # per-step sample: the oracle's measured rate on a calibration call sets
@@ -343,7 +363,7 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "layout": "aos", "sample_nnz": m},
         "cpu_baseline": {"value": value, "unit": "GNNZ/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {m} of {t.nnz} nonzeros per step"},
+                         "sample": f"first {m} of {full} nonzeros per step"},
         "e2e": {"value": value, "unit": "GNNZ/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -355,7 +375,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="allbutone_4way_1000", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="single_5way_zipf", choices=sorted(WORKLOADS))
     ap.add_argument("--path", default="auto")
     ap.add_argument("--accum", default="fp64", choices=["fp64", "compensated", "exact"])
     ap.add_argument("--layout", default="soa", choices=["soa", "aos"])
@@ -552,6 +572,20 @@ def main():
     }
     if prep_info:
         line["prepared"] = prep_info
+    if args.workload in STEP_ROOFLINE and not args.prepared:
+        # several kernels of comparable weight: the roofline is the step's
+        # (algorithmic bytes of one TTV over the step time); the dominant
+        # kernel's own rate, on the bytes one launch of it moves, stays beside it
+        line["dominant_kernel"] = dict(line["roofline"])
+        line["dominant_kernel"]["bytes_basis"] = ("bytes one launch of this kernel moves (not the TTV's "
+                                                  "algorithmic bytes)")
+        step_gbs = ab["total"] / (ms_step * 1e-3) / 1e9
+        line["roofline"] = {
+            "bound": "hbm", "kernel": "whole step: " + " + ".join(sorted(per_kernel)), "achieved": step_gbs,
+            "peak": peak, "unit": "GB/s", "frac": step_gbs / peak, "traffic": STEP_TRAFFIC.get(args.workload),
+            "peak_source": f"{peak_src} hbm_gbs",
+            "alg_bytes_per_step": ab["total"],
+            "alg_bytes_basis": "nnz*(8d+w) + vector once + nnz_out*(8*order+8)"}
 
     # ---- end to end: host buffers through the public call ----
     if rank == 0 or world > 1:

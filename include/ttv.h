@@ -426,8 +426,10 @@ void ttv_server_destroy(ttv_server *server);
  * is part of the library and stays resident on every GPU that loads it until
  * the process exits.
  *   - Limit: prod shape[R] <= 16384 cells (the dense path's shared-memory
- *     accumulator); larger result spaces return TTV_ERR_UNSUPPORTED, and a
- *     result larger than the fixed scratch returns TTV_ERR_BUDGET.
+ *     accumulator); larger result spaces return TTV_ERR_UNSUPPORTED.  The
+ *     fixed scratch holds at least 31 partial arrays of that largest size, so
+ *     TTV_ERR_BUDGET (kept as a guard) cannot occur at these limits; for
+ *     large results the call runs fewer CTAs, as many as the scratch holds.
  *   - vec_lens may be NULL; otherwise a mismatch returns TTV_ERR_VEC_LEN.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
@@ -461,6 +463,23 @@ int ttv_profile_get(const char *kernel, double *total_ms, long long *launches);
 int ttv_profile_names(char *buf, size_t len);
 /* Clears the per-kernel totals. */
 void ttv_profile_reset(void);
+
+/* ---- test hooks for the bounded device waits ----------------------------
+ * Every wait of a kernel on another CTA's progress (the sort's decoupled
+ * look-back across tiles, the staged dense kernel's bulk-copy pipeline) gives
+ * up after a poll limit, raises a timeout bit that the call turns into
+ * TTV_ERR_TIMEOUT, and lets the kernel finish without hanging.  These hooks
+ * let a test make such a wait run out on purpose (the paper has no
+ * counterpart; they exist only to test that error path). */
+/* polls >= 0: those waits give up after `polls` polls (0: at once); polls < 0
+ * restores their own limits.  Affects every later call in the process; a call
+ * that runs out returns TTV_ERR_TIMEOUT and its result is not valid. */
+int ttv_test_set_wait_polls(long long polls);
+/* One thread waits `polls` polls on an mbarrier that nothing arrives on
+ * (kind 0) or on a device word that nothing sets (kind 1).  Returns
+ * TTV_ERR_TIMEOUT when the wait ran out (the expected outcome), TTV_OK if it
+ * did not, TTV_ERR_ARG for another kind. */
+int ttv_test_wait_probe(int kind, unsigned int polls);
 
 #ifdef __cplusplus
 }

@@ -351,6 +351,27 @@ def launch_count() -> int:
     return int(_declare_prof(load()).ttv_launch_count())
 
 
+def test_set_wait_polls(polls: int):
+    """Test hook (ttv_test_set_wait_polls): the sort's look-back waits and the
+    staged dense kernel's pipeline waits give up after ``polls`` polls;
+    ``polls < 0`` restores their own limits."""
+    lib = load()
+    lib.ttv_test_set_wait_polls.argtypes = [ctypes.c_longlong]
+    lib.ttv_test_set_wait_polls.restype = ctypes.c_int
+    _check(lib, lib.ttv_test_set_wait_polls(int(polls)))
+
+
+def test_wait_probe(kind: int, polls: int) -> str:
+    """Test hook (ttv_test_wait_probe): one wait that nothing satisfies, on an
+    mbarrier (kind 0) or a device word (kind 1); returns the status name
+    ("TTV_ERR_TIMEOUT" when the wait ran out)."""
+    lib = load()
+    lib.ttv_test_wait_probe.argtypes = [ctypes.c_int, ctypes.c_uint]
+    lib.ttv_test_wait_probe.restype = ctypes.c_int
+    rc = lib.ttv_test_wait_probe(int(kind), int(polls))
+    return "TTV_OK" if rc == 0 else ERR.get(rc, str(rc))
+
+
 def profile_enable(on: bool = True):
     _declare_prof(load()).ttv_profile_enable(1 if on else 0)
 
@@ -730,7 +751,7 @@ def ttv_dense_noalloc(subs: torch.Tensor, vals: torch.Tensor, shape, modes, vecs
         lib.ttv_dense_noalloc.restype = ctypes.c_int
         lib._noalloc_declared = True
     modes = [int(m) for m in modes]
-    if out.dtype != torch.float64 or not out.is_cuda or (out.numel() > 1 and out.stride(-1) != 1):
+    if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
         raise ValueError("out must be a contiguous float64 CUDA buffer")
     vdt = vecs[0].dtype
     t = make_tensor(subs, vals, shape)

@@ -73,7 +73,6 @@ size_t bucket_workspace_bytes(int64_t nnz, int key_bits);
 void launch_bucket(const StreamDesc& p, int key_bits, void* ws, int64_t* out_subs, double* out_vals,
                    int64_t cap_rows, cudaStream_t stream);
 
-constexpr int64_t kDenseMaxCells = 16384;       // key spaces accumulated in shared memory
 constexpr size_t kVecSmemMax = 64 * 1024;       // staged vector bytes per CTA
 constexpr int64_t kMaxSortN = (1ll << 30) - 1;  // 30-bit counts in the look-back words
 

@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_dense_tma(StreamDesc p, int6
             int64_t i = 0;
             for (; i < ntiles; ++i) {
                 const int s = (int)(i % S);
-                if (i >= S && !mbar_wait(&empty[s], (uint32_t)(((i / S) - 1) & 1))) {
+                if (i >= S && !mbar_wait(&empty[s], (uint32_t)(((i / S) - 1) & 1), wait_limit(1u << 24))) {
                     set_error(p.status, kErrTimeout);
                     s_err = 1;
                     break;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_dense_tma(StreamDesc p, int6
         // consumers: two nonzeros of every tile per thread
         for (int64_t i = 0; i < ntiles; ++i) {
             const int s = (int)(i % S);
-            if (!mbar_wait(&full[s], (uint32_t)((i / S) & 1))) {
+            if (!mbar_wait(&full[s], (uint32_t)((i / S) & 1), wait_limit(1u << 24))) {
                 set_error(p.status, kErrTimeout);
                 s_err = 1;
                 break;
@@ -441,6 +441,45 @@ void launch_dense_vec(const StreamDesc& p, int want_presence, int G, double* par
     TTV_LAUNCH("dense_accum", stream,
                k<<<G, kVecThreads, smem, stream>>>(p, chunk, want_presence, pres_off, vec_off, partials,
                                                    pres_partials));
+}
+
+cudaError_t dense_vec_set_wait_override(uint32_t v) { return set_wait_override_here(v); }
+
+// ---- test hook: a wait that must run out -------------------------------------
+// One thread waits, with the given poll limit, on an mbarrier that nothing
+// arrives on (kind 0) or on a global word that nothing sets (kind 1), and
+// raises kErrTimeout when the wait runs out.  No copy is in flight, so the
+// CTA may simply return.
+__global__ void k_wait_probe(int kind, uint32_t polls, const uint32_t* word, Status* st) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    bool ok;
+    if (kind == 0) {
+        mbar_init(&bar, 1);
+        ok = mbar_wait(&bar, 0, polls);
+    } else {
+        uint32_t v = 0;
+        ok = spin_until(word, v, [](uint32_t x) { return x != 0u; }, polls);
+    }
+    if (!ok) set_error(st, kErrTimeout);
+}
+
+// 1: the wait ran out (status raised), 0: it did not; negative: CUDA error.
+int wait_probe(int kind, uint32_t polls, cudaStream_t stream) {
+    Status* st = nullptr;
+    if (cudaMalloc(&st, sizeof(Status) + 256) != cudaSuccess) return -1;
+    uint32_t* word = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(st) + sizeof(Status));
+    int rc = -1;
+    Status h;
+    if (cudaMemsetAsync(st, 0, sizeof(Status) + 256, stream) == cudaSuccess) {
+        TTV_LAUNCH("wait_probe", stream, k_wait_probe<<<1, 32, 0, stream>>>(kind, polls, word, st));
+        if (cudaGetLastError() == cudaSuccess &&
+            cudaMemcpyAsync(&h, st, sizeof(Status), cudaMemcpyDeviceToHost, stream) == cudaSuccess &&
+            cudaStreamSynchronize(stream) == cudaSuccess)
+            rc = (h.err & kErrTimeout) ? 1 : 0;
+    }
+    cudaFree(st);
+    return rc;
 }
 
 }  // namespace ttv

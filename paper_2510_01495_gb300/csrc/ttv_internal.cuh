@@ -11,6 +11,8 @@
 
 namespace ttv {
 
+constexpr int64_t kDenseMaxCells = 16384;       // key spaces accumulated in shared memory
+
 constexpr int kMaxD = TTV_MAX_D;
 
 // Error bits accumulated in Status::err by kernels (host maps them to codes).
@@ -295,6 +297,20 @@ __device__ __forceinline__ void delinearise(const StreamDesc& p, uint64_t key, i
         out_row[j] = (int64_t)(key - q * n);
         key = q;
     }
+}
+
+// ---- test hook: shortened wait limits ---------------------------------------
+// 0 (the default): every bounded wait keeps its own poll limit.  v > 0: the
+// waits that read wait_limit() give up after v - 1 polls, so that a test can
+// make them run out on purpose and check the error status that follows.
+// Each translation unit holds its own copy; ttv_test_set_wait_polls sets all.
+static __device__ uint32_t g_wait_override = 0;
+__device__ __forceinline__ uint32_t wait_limit(uint32_t dflt) {
+    const uint32_t o = *reinterpret_cast<const volatile uint32_t*>(&g_wait_override);
+    return o ? o - 1 : dflt;
+}
+static inline cudaError_t set_wait_override_here(uint32_t v) {
+    return cudaMemcpyToSymbol(g_wait_override, &v, sizeof v);
 }
 
 // Bounded spin on a 32-bit word until pred(value) holds; false on timeout.

@@ -31,6 +31,10 @@ int cuda_fail(cudaError_t e, const char* what);
 
 constexpr size_t kNoAllocScratchBytes = TTV_NOALLOC_SCRATCH_BYTES;
 constexpr size_t kNoAllocStatusBytes = 256;
+// The scratch holds many partial arrays of the largest dense result, so the
+// budget check below is a guard that the documented limits never reach.
+static_assert(kNoAllocScratchBytes >= kNoAllocStatusBytes + 31 * kDenseMaxCells * sizeof(double),
+              "fixed scratch smaller than 31 partial arrays of the largest dense result");
 
 // The scratch array.  In host code this name is only a host-side stand-in:
 // its device address must be fetched with cudaGetSymbolAddress.

@@ -2,6 +2,7 @@
 // Every kernel launch of the library goes through prof_begin/prof_end.  When
 // profiling is enabled, an event pair brackets the launch on its own stream
 // and ttv_profile_collect() folds the elapsed times into per-kernel totals.
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <map>
@@ -57,11 +58,29 @@ void prof_end(cudaStream_t s) {
     t_open = Pending{nullptr, nullptr, nullptr};
 }
 
+cudaError_t sort_set_wait_override(uint32_t v);
+cudaError_t dense_vec_set_wait_override(uint32_t v);
+int wait_probe(int kind, uint32_t polls, cudaStream_t stream);
+
 }  // namespace ttv
 
 using namespace ttv;
 
 extern "C" {
+
+int ttv_test_set_wait_polls(long long polls) {
+    const uint32_t v = polls < 0 ? 0u : (uint32_t)std::min<long long>(polls, 0xFFFFFFFELL) + 1u;
+    if (sort_set_wait_override(v) != cudaSuccess || dense_vec_set_wait_override(v) != cudaSuccess)
+        return TTV_ERR_CUDA;
+    return TTV_OK;
+}
+
+int ttv_test_wait_probe(int kind, unsigned int polls) {
+    if (kind != 0 && kind != 1) return TTV_ERR_ARG;
+    const int r = wait_probe(kind, polls, nullptr);
+    if (r < 0) return TTV_ERR_CUDA;
+    return r ? TTV_ERR_TIMEOUT : TTV_OK;
+}
 
 long long ttv_launch_count(void) { return g_launches.load(); }
 

@@ -206,11 +206,12 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const uint64_t* __
     } else {
         st_relaxed(my, kFlagAgg | cnt);
         int64_t j = (int64_t)tile - 1;
+        const uint32_t polls = wait_limit(1u << 24);
         while (j >= 0) {
             const uint32_t* q = lookback + (size_t)j * kRadix + tid;
             uint32_t val = 0;
             bool ok = false;
-            for (uint32_t it = 0; it < (1u << 24); ++it) {
+            for (uint32_t it = 0; it < polls; ++it) {
                 val = ld_relaxed(q);
                 if (val & (kFlagAgg | kFlagInc)) { ok = true; break; }
                 if (it > 32) __nanosleep(32);
@@ -234,10 +235,13 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const uint64_t* __
         const uint64_t kk = sm.keys[j];
         const uint32_t d = (uint32_t)(kk >> shift) & (kRadix - 1);
         const uint32_t out = sm.gbase[d] + (uint32_t)j - sm.tile_start[d];
+        if ((int64_t)out >= n) continue;     // only after a look-back ran out: offsets are then unreliable
         keys_out[out] = kk;
         vals_out[out] = sm.vals[j];
     }
 }
+
+cudaError_t sort_set_wait_override(uint32_t v) { return set_wait_override_here(v); }
 
 size_t sort_workspace_bytes(int64_t n, int bits) {
     const int npass = bits <= 0 ? 0 : (bits + kRadixBits - 1) / kRadixBits;

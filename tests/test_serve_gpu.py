@@ -1,5 +1,6 @@
-"""The continuous-batching server: every result in the mix equals the result
-of the same TTV run alone (ttv_multi), within the FP64 tolerance; budget
+"""The continuous-batching server: every result in the mix matches the oracle
+and equals the result of the same TTV run alone (ttv_multi), within the FP64
+tolerance; budget
 admission and refusal; bounded waits."""
 import threading
 
@@ -52,19 +53,18 @@ def test_server_mix_equals_alone(cuda_lib):
     for t in th:
         t.join()
     results = [srv.wait(r, timeout_us=60_000_000) for r in rids]
-    for (ti, modes, vecs), res in zip(reqs, results):
+    for k, ((ti, modes, vecs), res) in enumerate(zip(reqs, results)):
         subs, vals, shape = tensors[ti]
+        # every served result against the oracle ...
+        ref, A = oracle_ttv(subs, vals, shape, modes, vecs)
+        check_result(res, ref, A, what=f"served request {k}")
+        # ... and against the same TTV run alone
         dv = [torch.from_numpy(v).to(dev) for v in vecs]
         alone = cuda_lib.ttv_multi(subs, vals, shape, modes, dv)
-        A = cuda_lib.ttv_multi(subs, vals.abs(), shape, modes, [v.abs() for v in dv])
+        check_result(alone, ref, A, what=f"request {k} alone")
         assert res.shape == alone.shape
         assert torch.equal(res.subs, alone.subs)
-        _close(res.vals, alone.vals, A.vals)
-    # one against the oracle as well
-    ti, modes, vecs = reqs[0]
-    subs, vals, shape = tensors[ti]
-    ref, A = oracle_ttv(subs, vals, shape, modes, vecs)
-    check_result(results[0], ref, A)
+        _close(res.vals, alone.vals, torch.from_numpy(A))
     st = srv.stats()
     assert st["completed"] == len(reqs) and st["pending"] == 0
     assert 0 < st["p50_us"] <= st["p99_us"] <= st["max_us"]
