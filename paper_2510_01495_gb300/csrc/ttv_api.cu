@@ -330,7 +330,10 @@ static int make_plan(const ttv_tensor* t, const int32_t* modes, int32_t n_v, con
     // The hash path sums in atomic arrival order: deterministic and
     // compensated requests go to the sort path.
     if (path == TTV_PATH_HASH && (want_exact || pl.compensated || !hash_applicable(p))) path = TTV_PATH_SORT;
-    if (path == TTV_PATH_BUCKET && (pl.dense_out || !bucket_applicable(p))) path = TTV_PATH_SORT;
+    // The partition path sums in arrival order: deterministic and compensated
+    // requests go to the sort path, like dense results and inputs it does not take.
+    if (path == TTV_PATH_BUCKET && (pl.dense_out || want_exact || pl.compensated || !bucket_applicable(p)))
+        path = TTV_PATH_SORT;
     if (force_sort && path == TTV_PATH_BUCKET) path = TTV_PATH_SORT;
     if (path == TTV_PATH_DENSE && !dense_ok) return fail(TTV_ERR_UNSUPPORTED, "dense path needs prod shape[R] <= %lld", (long long)kDenseMaxCells);
     if (path == TTV_PATH_DENSE) {
@@ -513,7 +516,7 @@ static int finalize(ttv_out* out) {
     if (h.err & kErrInternal) return s->rc = fail(TTV_ERR_CUDA, "internal device check failed");
     if (h.err & kErrRetry) {
         s->retry_sort = 1;
-        return s->rc = fail(TTV_ERR_UNSUPPORTED, "bucket path could not place every pair");
+        return s->rc = fail(TTV_ERR_UNSUPPORTED, "partition path: a bucket outgrew its sampled capacity");
     }
     if (h.err & kErrNonFinite) {
         s->nonfinite = 1;

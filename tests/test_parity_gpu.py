@@ -197,6 +197,25 @@ def test_bucket_path_zipf(cuda_lib, layout):
     run_case(cuda_lib, p, path="bucket", layout=layout)
 
 
+@pytest.mark.parametrize("layout", ["soa", "aos"])
+def test_partition_path_runs_without_fallback(cuda_lib, layout):
+    # the partition path itself (not the sort path it falls back to) produced the result
+    p = S.single_5way_zipf(nnz=2_000_000, shape=(2000, 500, 10000, 200, 50))
+    subs, vals, vecs = to_device(p, layout=layout)
+    ref, A = oracle_ttv(subs, vals, p.tensor.shape, p.modes, vecs)
+    cuda_lib.profile_reset()
+    cuda_lib.profile_enable(True)
+    try:
+        res = cuda_lib.ttv_multi(subs, vals, p.tensor.shape, p.modes, vecs, path="bucket")
+    finally:
+        cuda_lib.profile_enable(False)
+    cuda_lib.profile_collect()
+    names = cuda_lib.profile_names()
+    assert "part_scatter" in names and "part_process" in names, names
+    assert "rbk_emit" not in names, names
+    check_result(res, ref, A, what="partition path")
+
+
 def test_bucket_path_large_uniform(cuda_lib):
     # 1.5e6 uniform nonzeros, 3-way result of 1.2e9 cells
     p = rand_problem(77, (1000, 1200, 50, 1000), 1_500_000, [2])
