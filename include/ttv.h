@@ -222,7 +222,8 @@ void ttv_batch_release(void);
  * candidate on the given problem -- accumulation path (DENSE, SORT, HASH,
  * BUCKET) x CTAs per SM of the streaming pass (2/3/4 for DENSE, 4/8/16 for
  * SORT, 8/16 for HASH) x nonzeros per thread per iteration (DENSE: 1 or 2
- * pairs, or 4 = the bulk-staged persistent kernel with one CTA per SM;
+ * pairs, 3 = one pair into warp-private accumulators where they fit, or
+ * 4 = the bulk-staged persistent kernel with one CTA per SM;
  * HASH: 2 or 4) -- `trials` times
  * after one warm-up run each, takes
  * the median of CUDA-event times on `stream`, and records the fastest for

@@ -919,13 +919,16 @@ int ttv_autotune(const ttv_tensor* t, const int32_t* modes, int32_t n_v, const v
     const uint64_t key = tune_key(p, base.dense_out);
 
     // candidates: path x CTAs per SM of the streaming pass x nonzeros per
-    // thread (DENSE: 1 or 2 pairs per iteration, or 4 = the bulk-staged
-    // persistent kernel, one CTA per SM; HASH: 2 or 4 per iteration)
+    // thread (DENSE: 1 or 2 pairs per iteration into one shared array, 3 =
+    // one pair into warp-private arrays (two CTAs per SM), or 4 = the
+    // bulk-staged persistent kernel, one CTA per SM; HASH: 2 or 4 per
+    // iteration)
     struct Cand { int path, ctas, items; };
     std::vector<Cand> cands;
     const bool dense_ok = (int64_t)p.nkeys <= kDenseMaxCells || base.order0;
     if (dense_ok) {
         cands.push_back({TTV_PATH_DENSE, 1, 4});
+        cands.push_back({TTV_PATH_DENSE, 2, 3});
         for (int it : {1, 2})
             for (int c : {2, 3, 4}) cands.push_back({TTV_PATH_DENSE, c, it});
     }

@@ -21,7 +21,7 @@ constexpr int kVecThreads = 256;
 // SM; the default) or 2 (more loads in flight per thread, 3 CTAs per SM);
 // the autotuner picks per problem class.
 
-template <int D, bool kIntP>
+template <int D, bool kIntP, bool kPriv = false>
 __device__ __forceinline__ void dense_item(const StreamDesc& p, const double* sv, const SigEntry* sve,
                                            const int64_t* s, double val, double* acc, uint32_t* pres,
                                            int want_presence) {
@@ -60,12 +60,23 @@ __device__ __forceinline__ void dense_item(const StreamDesc& p, const double* sv
             else key += (uint64_t)s[m] * p.kstride[m];
         }
     }
-    atomicAdd(&acc[key], t);
+    if constexpr (kPriv) {
+        // the warp's own accumulator: a plain add unless another active lane
+        // of the warp hits the same cell in this step
+        const uint32_t same = __match_any_sync(__activemask(), (uint32_t)key);
+        if (__popc(same) == 1) acc[key] += t;
+        else atomicAdd(&acc[key], t);
+    } else {
+        atomicAdd(&acc[key], t);
+    }
     if (want_presence) atomicOr(&pres[key >> 5], 1u << (key & 31));
 }
 
+// kVecPairs == 3: one pair per iteration into warp-private accumulators
+// (eight arrays of P cells per CTA, two CTAs per SM): the binary64 add is a
+// plain read-modify-write instead of a compare-and-swap loop.
 template <int D, bool kSoA, bool kIntP, int kVecPairs>
-__global__ void __launch_bounds__(kVecThreads, kVecPairs == 1 ? 4 : 3) k_dense_vec(StreamDesc p, int64_t chunk, int want_presence,
+__global__ void __launch_bounds__(kVecThreads, kVecPairs == 1 ? 4 : (kVecPairs == 2 ? 3 : 2)) k_dense_vec(StreamDesc p, int64_t chunk, int want_presence,
                                                            size_t pres_off, size_t vec_off,
                                                            double* __restrict__ partials,
                                                            uint32_t* __restrict__ pres_partials) {
@@ -74,9 +85,13 @@ __global__ void __launch_bounds__(kVecThreads, kVecPairs == 1 ? 4 : 3) k_dense_v
     uint32_t* pres = reinterpret_cast<uint32_t*>(dsm + pres_off);
     double* sv = reinterpret_cast<double*>(dsm + vec_off);
     SigEntry* sve = reinterpret_cast<SigEntry*>(dsm + vec_off);
+    constexpr bool kPriv = kVecPairs == 3;
+    constexpr int kPairs = kPriv ? 1 : kVecPairs;
+    constexpr int kCopies = kPriv ? kVecThreads / 32 : 1;
     const int64_t P = (int64_t)p.nkeys;
     const int64_t npres = (P + 31) / 32;
-    for (int64_t i = threadIdx.x; i < P; i += kVecThreads) acc[i] = 0.0;
+    for (int64_t i = threadIdx.x; i < P * kCopies; i += kVecThreads) acc[i] = 0.0;
+    double* wacc = acc + (kPriv ? (int64_t)(threadIdx.x >> 5) * P : 0);
     if (want_presence)
         for (int64_t i = threadIdx.x; i < npres; i += kVecThreads) pres[i] = 0u;
     if (kIntP) stage_vectors_sig(p, sve);
@@ -89,12 +104,12 @@ __global__ void __launch_bounds__(kVecThreads, kVecPairs == 1 ? 4 : 3) k_dense_v
     const double* vd = static_cast<const double*>(p.vals);
     const float* vf = static_cast<const float*>(p.vals);
 
-    for (int64_t q0 = threadIdx.x; q0 < npairs; q0 += (int64_t)kVecThreads * kVecPairs) {
-        int64_t s[kVecPairs][2][D];
-        double v[kVecPairs][2];
-        bool ok[kVecPairs];
+    for (int64_t q0 = threadIdx.x; q0 < npairs; q0 += (int64_t)kVecThreads * kPairs) {
+        int64_t s[kPairs][2][D];
+        double v[kPairs][2];
+        bool ok[kPairs];
 #pragma unroll
-        for (int u = 0; u < kVecPairs; ++u) {
+        for (int u = 0; u < kPairs; ++u) {
             const int64_t q = q0 + (int64_t)u * kVecThreads;
             ok[u] = q < npairs;
             if (!ok[u]) continue;
@@ -127,10 +142,10 @@ __global__ void __launch_bounds__(kVecThreads, kVecPairs == 1 ? 4 : 3) k_dense_v
             }
         }
 #pragma unroll
-        for (int u = 0; u < kVecPairs; ++u) {
+        for (int u = 0; u < kPairs; ++u) {
             if (!ok[u]) continue;
-            dense_item<D, kIntP>(p, sv, sve, s[u][0], v[u][0], acc, pres, want_presence);
-            dense_item<D, kIntP>(p, sv, sve, s[u][1], v[u][1], acc, pres, want_presence);
+            dense_item<D, kIntP, kPriv>(p, sv, sve, s[u][0], v[u][0], wacc, pres, want_presence);
+            dense_item<D, kIntP, kPriv>(p, sv, sve, s[u][1], v[u][1], wacc, pres, want_presence);
         }
     }
     // odd tail of the last chunk
@@ -140,11 +155,16 @@ __global__ void __launch_bounds__(kVecThreads, kVecPairs == 1 ? 4 : 3) k_dense_v
 #pragma unroll
         for (int m = 0; m < D; ++m) s1[m] = p.subs[k * p.snz + m * p.smode];
         const double v1 = p.val_f32 ? (double)vf[k] : vd[k];
-        dense_item<D, kIntP>(p, sv, sve, s1, v1, acc, pres, want_presence);
+        dense_item<D, kIntP, kPriv>(p, sv, sve, s1, v1, wacc, pres, want_presence);
     }
     __syncthreads();
     double* my = partials + (size_t)blockIdx.x * P;
-    for (int64_t i = threadIdx.x; i < P; i += kVecThreads) my[i] = acc[i];
+    for (int64_t i = threadIdx.x; i < P; i += kVecThreads) {
+        double x = acc[i];
+#pragma unroll
+        for (int c = 1; c < kCopies; ++c) x += acc[c * P + i];     // fixed order
+        my[i] = x;
+    }
     if (want_presence) {
         uint32_t* mp = pres_partials + (size_t)blockIdx.x * npres;
         for (int64_t i = threadIdx.x; i < npres; i += kVecThreads) mp[i] = pres[i];
@@ -345,10 +365,33 @@ static DenseVecKernel pick_p(bool soa, bool intp) {
 
 template <int D>
 static DenseVecKernel pick(bool soa, bool intp, int pairs) {
-    return pairs == 2 ? pick_p<D, 2>(soa, intp) : pick_p<D, 1>(soa, intp);
+    return pairs == 3 ? pick_p<D, 3>(soa, intp) : pairs == 2 ? pick_p<D, 2>(soa, intp) : pick_p<D, 1>(soa, intp);
 }
 
-static int dense_vec_pairs(const StreamDesc& p) { return p.items == 2 ? 2 : 1; }
+int dense_vec_products_int(const StreamDesc& p);
+
+// Accumulator layout: 1 = one shared array per CTA (binary64 atomics; the
+// default), 2 = the same with two pairs per thread per iteration, 3 = one
+// array per warp with plain adds (an autotuner candidate where the eight
+// copies, the staged vectors and no presence bits fit in half an SM's shared
+// memory).  On the all-but-one 1000^4 problem mode 3 takes 173 us against
+// mode 1's 105 us: the binary64 compare-and-swap adds cost less than the
+// halved occupancy.
+constexpr size_t kPrivSmemMax = 110 * 1024;
+
+static int dense_vec_mode(const StreamDesc& p, int want_presence) {
+    if (p.items == 2) return 2;
+    if (p.items == 3) {
+        const size_t vec = (size_t)p.vtotal * (dense_vec_products_int(p) ? sizeof(SigEntry) : sizeof(double));
+        const size_t priv = (size_t)p.nkeys * sizeof(double) * (kVecThreads / 32) + 16 + vec;
+        if (!want_presence && priv <= kPrivSmemMax) return 3;
+    }
+    return 1;
+}
+
+static size_t dense_vec_acc_bytes(const StreamDesc& p, int want_presence) {
+    return (size_t)p.nkeys * sizeof(double) * (dense_vec_mode(p, want_presence) == 3 ? kVecThreads / 32 : 1);
+}
 
 static DenseVecKernel dense_vec_kernel(int d, bool soa, bool intp, int pairs) {
     switch (d) {
@@ -375,14 +418,12 @@ bool dense_vec_applicable(const StreamDesc& p) {
 int dense_vec_products_int(const StreamDesc& p) { return __builtin_popcount(p.smask) >= 2; }
 
 size_t dense_vec_smem(const StreamDesc& p, int want_presence) {
-    size_t off = (size_t)p.nkeys * sizeof(double);
+    size_t off = dense_vec_acc_bytes(p, want_presence);
     if (want_presence) off += ((p.nkeys + 31) / 32) * sizeof(uint32_t);
     off = (off + 15) & ~size_t(15);
     off += (size_t)p.vtotal * (dense_vec_products_int(p) ? sizeof(SigEntry) : sizeof(double));
     return off;
 }
-
-int dense_vec_products_int(const StreamDesc& p);
 
 // The bulk-staged kernel is the autotuner's items == 4 candidate, used when
 // at least two stages fit beside the accumulator and the staged vectors and
@@ -405,14 +446,15 @@ static int64_t tma_chunk(const StreamDesc& p, int G) {
 int dense_vec_grid(const StreamDesc& p, int want_presence) {
     if (use_tma(p, want_presence)) return num_sms();
     const bool soa = p.snz == 1;
-    DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p), dense_vec_pairs(p));
+    const int mode = dense_vec_mode(p, want_presence);
+    DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p), mode);
     const size_t smem = dense_vec_smem(p, want_presence);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kVecThreads, smem);
     per_sm = std::max(1, std::min(per_sm, p.ctas_per_sm > 0 ? p.ctas_per_sm : 4));
-    const int64_t min_chunk = std::max<int64_t>((int64_t)kVecThreads * dense_vec_pairs(p) * 2 * 4, (int64_t)p.nkeys * 4);
+    const int64_t min_chunk = std::max<int64_t>((int64_t)kVecThreads * (mode == 2 ? 2 : 1) * 2 * 4, (int64_t)p.nkeys * 4);
     const int64_t by_work = std::max<int64_t>(1, (p.nnz + min_chunk - 1) / min_chunk);
     return (int)std::max<int64_t>(1, std::min<int64_t>(by_work, (int64_t)num_sms() * per_sm));
 }
@@ -430,9 +472,9 @@ void launch_dense_vec(const StreamDesc& p, int want_presence, int G, double* par
                                                           pres_partials));
         return;
     }
-    DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p), dense_vec_pairs(p));
+    DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p), dense_vec_mode(p, want_presence));
     const size_t smem = dense_vec_smem(p, want_presence);
-    size_t pres_off = (size_t)p.nkeys * sizeof(double);
+    size_t pres_off = dense_vec_acc_bytes(p, want_presence);
     size_t vec_off = pres_off + (want_presence ? ((p.nkeys + 31) / 32) * sizeof(uint32_t) : 0);
     vec_off = (vec_off + 15) & ~size_t(15);
     int64_t chunk = (p.nnz + G - 1) / G;
