@@ -394,6 +394,7 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="nnz scale for batch_512 / serve_64")
     ap.add_argument("--requests", type=int, default=2000, help="serve_64: requests in the timed stream")
     ap.add_argument("--rate", type=float, default=20000.0, help="serve_64: Poisson arrival rate (req/s)")
+    ap.add_argument("--light-rate", type=float, default=200.0, help="serve_64: arrival rate of the light-load leg")
     args = ap.parse_args()
     if args.seed == 0:
         args.seed = {"allbutone_4way_1000": 2, "single_5way_zipf": 3, "single_3way_100": 1, "batch_512": 5,
@@ -751,29 +752,57 @@ def run_serve(args, rank, world, local_rank):
         m = int(g.integers(0, 4))
         reqs.append((ti, m, g.uniform(-1, 1, shapes[ti][m]).astype(np.float32)))
     for ti, m, x in reqs[:64]:
-        srv.wait(srv.submit(ids[ti], [m], [x], accum="compensated"))
-        plain.wait(plain.submit(pids[ti], [m], [x], accum="compensated"))
+        srv.wait(srv.submit(ids[ti], [m], [x], accum="compensated"), timeout_us=120_000_000)
+        plain.wait(plain.submit(pids[ti], [m], [x], accum="compensated"), timeout_us=120_000_000)
     srv.reset_stats()
     clocks = _clock_start(local_rank)
     arrivals = np.cumsum(g.exponential(1.0 / args.rate, size=args.requests))
 
-    def stream(accum):
-        rids = []
+    def stream(accum, arr=None, items=None):
+        # the client takes every result as soon as it is ready (a waiter
+        # thread, in submission order), so results do not pile up on the device
+        import queue
+        arr = arrivals if arr is None else arr
+        items = reqs[64:] if items is None else items
+        pending = queue.Queue()
+        errors = []
+
+        def waiter():
+            while True:
+                rid = pending.get()
+                if rid is None:
+                    return
+                try:
+                    srv.wait(rid, timeout_us=120_000_000)
+                except Exception as e:   # noqa: BLE001 -- re-raised by the submitting thread
+                    errors.append(e)
+
+        th = threading.Thread(target=waiter)
         barrier(dist)
         t0 = time.perf_counter()
-        for k, (ti, m, x) in enumerate(reqs[64:]):
-            delay = arrivals[k] - (time.perf_counter() - t0)
+        th.start()
+        for k, (ti, m, x) in enumerate(items):
+            delay = arr[k] - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            rids.append(srv.submit(ids[ti], [m], [x], accum=accum))
-        for r in rids:
-            srv.wait(r)
+            pending.put(srv.submit(ids[ti], [m], [x], accum=accum))
+        pending.put(None)
+        th.join()
+        if errors:
+            raise errors[0]
         w = time.perf_counter() - t0
         barrier(dist)
         return max_over_ranks(dist, w, dev)
 
     wall = stream("compensated")
     st = srv.stats()
+    # light load: the same requests arriving at --light-rate, where a request
+    # rarely waits for another; its latency against the one-at-a-time form
+    n_light = min(300, args.requests)
+    srv.reset_stats()
+    light_arr = np.cumsum(g.exponential(1.0 / args.light_rate, size=n_light))
+    stream("compensated", light_arr, reqs[64:64 + n_light])
+    st_l = srv.stats()
     # the same stream on prepared layouts (every mode of every tensor, as far
     # as the budget allows), the same compensated accumulation
     t_prep = time.perf_counter()
@@ -787,7 +816,7 @@ def run_serve(args, rank, world, local_rank):
                 pass
     t_prep = time.perf_counter() - t_prep
     for ti, m, x in reqs[:64]:
-        srv.wait(srv.submit(ids[ti], [m], [x], accum="compensated"))
+        srv.wait(srv.submit(ids[ti], [m], [x], accum="compensated"), timeout_us=120_000_000)
     srv.reset_stats()
     wall_p = stream("compensated")
     st_p = srv.stats()
@@ -797,7 +826,7 @@ def run_serve(args, rank, world, local_rank):
     plain.reset_stats()
     t1 = time.perf_counter()
     for ti, m, x in reqs[64:64 + n_plain]:
-        plain.wait(plain.submit(pids[ti], [m], [x], accum="compensated"))
+        plain.wait(plain.submit(pids[ti], [m], [x], accum="compensated"), timeout_us=120_000_000)
     wall_plain = time.perf_counter() - t1
     pst = plain.stats()
     plain_nnz = sum(nnzs[ti] for ti, _, _ in reqs[64:64 + n_plain])
@@ -808,7 +837,7 @@ def run_serve(args, rank, world, local_rank):
     for sb, v64, shp, ti in acc_sample:
         m = int(g.integers(0, 4))
         x64 = g.uniform(-1, 1, shp[m])
-        r32 = srv.wait(srv.submit(ids[ti], [m], [x64.astype(np.float32)], accum="compensated"))
+        r32 = srv.wait(srv.submit(ids[ti], [m], [x64.astype(np.float32)], accum="compensated"), timeout_us=120_000_000)
         xd = torch.from_numpy(x64).to(dev)
         r64 = ttv.ttv_multi(sb, v64, shp, [m], [xd], accum="compensated")
         ra = ttv.ttv_multi(sb, v64.abs(), shp, [m], [xd.abs()], accum="compensated")
@@ -834,6 +863,8 @@ def run_serve(args, rank, world, local_rank):
                    "budget_bytes": 60 << 30},
         "serve": {"p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
                   "throughput_rps": args.requests * world / wall, "completed": st["completed"]},
+        "serve_light": {"rate_req_s": args.light_rate, "requests": n_light, "p50_ms": st_l["p50_us"] / 1e3,
+                        "p99_ms": st_l["p99_us"] / 1e3},
         "serve_prepared": {"p50_ms": st_p["p50_us"] / 1e3, "p99_ms": st_p["p99_us"] / 1e3,
                            "throughput_rps": args.requests * world / wall_p,
                            "throughput_gnnz_s": sum_over_ranks(dist, sum(nnzs[ti] for ti, _, _ in reqs[64:]), dev)

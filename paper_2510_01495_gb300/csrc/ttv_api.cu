@@ -770,7 +770,12 @@ static void init_once() {
         cudaGetDevice(&dev);
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-            uint64_t thr = UINT64_MAX;
+            // Keep up to this much freed memory in the stream-ordered pool
+            // for reuse (no release and re-map between calls), and give the
+            // rest back at synchronisation points: with no limit a stream of
+            // calls of varying sizes on several streams grows the pool until
+            // the device runs out.
+            uint64_t thr = 8ull << 30;
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
         }
     });

@@ -19,6 +19,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -69,6 +70,7 @@ struct Request {
     void* dvecs = nullptr;
     ttv_out out{};
     int rc = TTV_OK;
+    std::string msg;                          // the library's message when rc != TTV_OK
     bool done = false;
     double latency_us = 0;
 };
@@ -118,11 +120,18 @@ void free_resident(Resident& r) {
 void complete(ttv_server* s, Slot& sl) {
     std::shared_ptr<Request> r = sl.req;
     sl.req.reset();
-    if (r->rc == TTV_OK) r->rc = ttv_out_sync(&r->out);
+    if (r->rc == TTV_OK) {
+        r->rc = ttv_out_sync(&r->out);
+        if (r->rc != TTV_OK) r->msg = ttv_last_error();
+    }
     // the result now belongs to the client: its buffers must not be touched here
     if (r->dvecs) cudaFreeAsync(r->dvecs, sl.stream);
     r->latency_us = std::chrono::duration<double, std::micro>(Clock::now() - r->submitted).count();
     std::lock_guard<std::mutex> g(s->mu);
+    // Admission runs ahead of the client's claims (a later, smaller request
+    // may start first), so the budget stops counting a request at completion:
+    // counting unclaimed results could block the very request a client waits
+    // for.  A client should take results as they finish.
     s->in_use -= r->need;
     r->done = true;
     s->running.erase(r->id);
@@ -174,6 +183,7 @@ void start(ttv_server* s, Slot& sl, const std::shared_ptr<Request>& r) {
     }
     if (e != cudaSuccess) {
         r->rc = ttv::cuda_fail(e, "request vectors");
+        r->msg = ttv_last_error();
     } else {
         std::vector<const void*> vp(r->modes.size());
         std::vector<int64_t> lens(r->modes.size());
@@ -207,11 +217,13 @@ void start(ttv_server* s, Slot& sl, const std::shared_ptr<Request>& r) {
                     }
             r->rc = ttv_prepared_run(prep->h, pv.data(), pl.data(), r->v_dtype, &r->out, &o,
                                      reinterpret_cast<ttv_stream_t>(sl.stream));
+            if (r->rc != TTV_OK) r->msg = ttv_last_error();
             std::lock_guard<std::mutex> g(s->mu);
             s->prepared_runs += 1;
         } else {
             r->rc = ttv_multi_checked(&tt, r->modes.data(), (int32_t)r->modes.size(), vp.data(), lens.data(),
                                       r->v_dtype, &r->out, &o, reinterpret_cast<ttv_stream_t>(sl.stream));
+            if (r->rc != TTV_OK) r->msg = ttv_last_error();
         }
     }
     cudaEventRecord(sl.done, sl.stream);
@@ -219,14 +231,24 @@ void start(ttv_server* s, Slot& sl, const std::shared_ptr<Request>& r) {
 
 void scheduler(ttv_server* s) {
     cudaSetDevice(s->device);
+    // While requests run, completions are polled without sleeping (a short
+    // sleep rounds up to the kernel's timer slack, tens of microseconds,
+    // which light-load latency would pay on every request); after this long
+    // without any completion or admission the loop backs off to short sleeps.
+    const auto spin_limit = std::chrono::microseconds(500);
+    Clock::time_point last_event = Clock::now();
     for (;;) {
         // completions (an error state also ends the request: it is reported, never waited on)
         for (Slot& sl : s->slots) {
             if (!sl.req) continue;
             const cudaError_t q = cudaEventQuery(sl.done);
             if (q == cudaErrorNotReady) continue;
-            if (q != cudaSuccess && sl.req->rc == TTV_OK) sl.req->rc = ttv::cuda_fail(q, "request");
+            if (q != cudaSuccess && sl.req->rc == TTV_OK) {
+                sl.req->rc = ttv::cuda_fail(q, "request");
+                sl.req->msg = ttv_last_error();
+            }
             complete(s, sl);
+            last_event = Clock::now();
         }
         std::unique_lock<std::mutex> lk(s->mu);
         if (s->stop && s->queue.empty()) {
@@ -259,13 +281,15 @@ void scheduler(ttv_server* s) {
         }
         bool any_running = false;
         for (Slot& sl : s->slots) any_running |= (bool)sl.req;
-        if (!started) {
-            if (any_running) {
-                lk.unlock();
-                std::this_thread::sleep_for(std::chrono::microseconds(5));
-            } else {
-                s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
-            }
+        if (started) {
+            last_event = Clock::now();
+        } else if (any_running) {
+            lk.unlock();
+            if (Clock::now() - last_event < spin_limit) std::this_thread::yield();
+            else std::this_thread::sleep_for(std::chrono::microseconds(20));
+        } else {
+            s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+            last_event = Clock::now();
         }
     }
 }
@@ -448,7 +472,8 @@ int ttv_server_wait(ttv_server* s, uint64_t req_id, int64_t timeout_us, ttv_out*
     s->finished.erase(req_id);
     *out = r->out;                       // ownership of the result moves to the caller
     memset(&r->out, 0, sizeof r->out);
-    if (r->rc != TTV_OK) return ttv::fail(r->rc, "request %llu failed (%d)", (unsigned long long)req_id, r->rc);
+    if (r->rc != TTV_OK)
+        return ttv::fail(r->rc, "request %llu failed (%d): %s", (unsigned long long)req_id, r->rc, r->msg.c_str());
     return TTV_OK;
 }
 
