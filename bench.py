@@ -99,9 +99,17 @@ DOMINANT = {"allbutone_4way_1000": [("dense_accum", _stream_bytes), ("dense_fx",
             "single_5way_zipf": [("onesweep", _pass_bytes), ("keys_terms", _stream_bytes)],
             "single_3way_100": [("dense_accum", _stream_bytes), ("dense_fx", _stream_bytes)]}
 
-# DRAM bytes of one whole step of the step-roofline workloads, from an ncu
-# capture (null until one is taken on the current sources).
-STEP_TRAFFIC = {}
+# DRAM bytes of one whole step of the step-roofline workloads (the sum of
+# dram__bytes_read.sum + dram__bytes_write.sum over the step's launches, from
+# the ncu launch list under profiles/), with the sha1 of the sources those
+# kernels are built from; reported as null once the sources differ.
+STEP_TRAFFIC = {
+    "single_5way_zipf": {
+        "files": ["ttv_keys.cu", "ttv_sort.cu", "ttv_internal.cuh", "ttv_udiv.h"],
+        "sha": "61e9c63b21d9",
+        "bytes_per_step": 30770329600,   # 12 launches of one TTV; 4.2x the algorithmic bytes
+    },
+}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel from an ncu capture of this workload (summary under profiles/), with
@@ -581,9 +589,13 @@ def main():
         line["dominant_kernel"]["bytes_basis"] = ("bytes one launch of this kernel moves (not the TTV's "
                                                   "algorithmic bytes)")
         step_gbs = ab["total"] / (ms_step * 1e-3) / 1e9
+        st_tr = STEP_TRAFFIC.get(args.workload)
+        step_traffic = None
+        if st_tr and default_cfg and kernel_source_hash(st_tr["files"]) == st_tr["sha"]:
+            step_traffic = st_tr["bytes_per_step"]
         line["roofline"] = {
             "bound": "hbm", "kernel": "whole step: " + " + ".join(sorted(per_kernel)), "achieved": step_gbs,
-            "peak": peak, "unit": "GB/s", "frac": step_gbs / peak, "traffic": STEP_TRAFFIC.get(args.workload),
+            "peak": peak, "unit": "GB/s", "frac": step_gbs / peak, "traffic": step_traffic,
             "peak_source": f"{peak_src} hbm_gbs",
             "alg_bytes_per_step": ab["total"],
             "alg_bytes_basis": "nnz*(8d+w) + vector once + nnz_out*(8*order+8)"}
