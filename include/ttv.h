@@ -179,18 +179,26 @@ int ttv_out_sync(ttv_out *out);
 
 /* Releases what the library allocated for `out` (not caller buffers). */
 void ttv_out_free(ttv_out *out);
+/* ttv_out_free on outs[0..n) (a batch's results): one call instead of n. */
+void ttv_outs_free(ttv_out *outs, int32_t n);
 
 /* Message for the calling thread's last error ("" if none). */
 const char *ttv_last_error(void);
 
 /* ---- batched TTV ------------------------------------------------------------
  * Many independent TTVs (paper Eq. 3 each) in one CUDA-graph launch.  The
- * first call with a given set of problems captures every problem's kernels
- * into one graph, spread over up to 8 concurrent streams (largest problems
- * first), and instantiates it; a later call with identical problems (same
- * pointers, sizes, modes, output buffers, workspace and options) launches the
- * cached graph without host work per problem.  Up to 16 graphs are cached;
- * ttv_batch_release() drops them. */
+ * first call with a given set of problems captures them into one graph and
+ * instantiates it; a later call with identical problems (same pointers,
+ * sizes, modes, output buffers, workspace and options) launches the cached
+ * graph without host work per problem.  Every problem whose plan is the sort
+ * path with a sparse result runs stage-wise: each stage (keys and terms per
+ * order and layout class, the digit-count scan, each 8-bit digit pass, the
+ * four reduce-by-key stages) is one launch over all such problems, so they
+ * cost about 20 launches together whatever their number.  The other problems
+ * (dense, hash and partition paths, dense results) keep their own launch
+ * sequences, spread over up to 7 concurrent streams beside it (largest
+ * problems first).  Up to 16 graphs are cached; ttv_batch_release() drops
+ * them. */
 typedef struct {
     ttv_tensor tensor;
     const int32_t *modes;        /* host, n_v contracted modes                    */

@@ -787,8 +787,34 @@ def _declare_batch(lib):
     lib.ttv_batch_graph_launches.restype = ctypes.c_longlong
     lib.ttv_batch_release.argtypes = []
     lib.ttv_batch_release.restype = None
+    lib.ttv_outs_free.argtypes = [P(Out), ctypes.c_int32]
+    lib.ttv_outs_free.restype = None
     lib._batch_declared = True
     return lib
+
+
+class BatchResults:
+    """The results of one batch run: ``Result`` views made on access."""
+
+    def __init__(self, meta, info):
+        self._meta, self._info = meta, info
+
+    def __len__(self):
+        return len(self._info)
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [self[j] for j in range(*i.indices(len(self)))]
+        ov, os_, _, _ = self._meta[i]
+        nn, dense, order, shp = self._info[i]
+        newshape = tuple(int(x) for x in shp[:order])
+        if dense:
+            return Result(None, ov[:nn].view(newshape), newshape, True)
+        subs_out = os_[:nn] if os_ is not None else torch.zeros((nn, 0), dtype=torch.int64, device=ov.device)
+        return Result(subs_out, ov[:nn], newshape, False)
+
+    def __iter__(self):
+        return (self[i] for i in range(len(self)))
 
 
 class Batch:
@@ -838,24 +864,17 @@ class Batch:
 
     def run(self, stream=None):
         """Launch the batch; returns one Result per problem (views of the
-        batch's buffers, rewritten by the next run)."""
-        outs = self._outs()
+        batch's buffers, rewritten by the next run), formed when indexed."""
+        if getattr(self, "_outs_arr", None) is None:
+            self._outs_arr = self._outs()      # the same caller buffers every run
+        outs = self._outs_arr
         rc = self.lib.ttv_batch(self.probs, self.n, outs, ctypes.byref(self.opts), _stream_handle(stream))
         try:
             _check(self.lib, rc)
-            res = []
-            for i, (ov, os_, shape, modes) in enumerate(self.meta):
-                newshape = tuple(int(outs[i].shape[j]) for j in range(outs[i].order))
-                nn = int(outs[i].nnz)
-                if outs[i].is_dense:
-                    res.append(Result(None, ov[:nn].view(newshape), newshape, True))
-                else:
-                    subs_out = os_[:nn] if os_ is not None else torch.zeros((nn, 0), dtype=torch.int64, device=ov.device)
-                    res.append(Result(subs_out, ov[:nn], newshape, False))
-            return res
+            return BatchResults(self.meta, [(int(o.nnz), bool(o.is_dense), int(o.order), tuple(o.shape))
+                                            for o in outs[:self.n]])
         finally:
-            for i in range(self.n):
-                self.lib.ttv_out_free(ctypes.byref(outs[i]))
+            self.lib.ttv_outs_free(outs, self.n)
 
     def graph_launches(self) -> int:
         """Kernel launches one replay of the cached graph performs."""

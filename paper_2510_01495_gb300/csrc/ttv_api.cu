@@ -417,7 +417,7 @@ static void layout(const Plan& pl, Arena& a, WsPtrs& w) {
     } else {
         const int64_t n = std::max<int64_t>(p.nnz, 1);
         const int npass = (pl.key_bits + 7) / 8;
-        const int64_t ntiles = (n + 4095) / 4096;
+        const int64_t ntiles = sort_tiles(n);
         w.sb.keys[0] = a.take<uint64_t>(n);
         w.sb.keys[1] = a.take<uint64_t>(n);
         w.sb.vals[0] = a.take<double>(n);
@@ -893,6 +893,11 @@ void ttv_out_free(ttv_out* out) {
     if (!s->borrowed_status) g_status_pool.release(s->hstatus);
     delete s;
     out->internal = nullptr;
+}
+
+void ttv_outs_free(ttv_out* outs, int32_t n) {
+    if (!outs) return;
+    for (int32_t i = 0; i < n; ++i) ttv_out_free(&outs[i]);
 }
 
 // ---- autotuner -----------------------------------------------------------------
@@ -1465,6 +1470,8 @@ struct BatchEntry {
     std::vector<ttv_out> shape;           // order, shape, is_dense, nnz of each result
     long long launches = 0;               // kernel nodes per replay
     void* arena = nullptr;                // library-owned workspace, if any
+    void* table = nullptr;                // job table of the batched sort path
+    int batched = 0;                      // problems on the batched sort path
     uint64_t last_use = 0;
 };
 
@@ -1518,21 +1525,226 @@ static void destroy_entry(BatchEntry* e) {
     if (e->exec) cudaGraphExecDestroy(e->exec);
     for (Status* s : e->status) g_status_pool.release(s);
     if (e->arena) cudaFree(e->arena);
+    if (e->table) cudaFree(e->table);
     delete e;
 }
 
+// ---- the batched sort path ---------------------------------------------------
+// Problems on the sort path with a sparse result and the order-specialised
+// key kernel run stage by stage: each stage is one launch over all of them
+// (batch_sort_capture), so a batch costs a fixed number of launches instead
+// of about a dozen per problem.  Their scratch that must start at zero (digit
+// counts, look-back words, pass tickets) sits in one region after the
+// per-problem workspaces and is cleared by one memset.
+static int plan_npass(const Plan& pl) { return (pl.key_bits + 7) / 8; }
+
+static bool batch_sortable(const Plan& pl) {
+    const StreamDesc& p = pl.desc;
+    const int npass = plan_npass(pl);
+    return pl.path == TTV_PATH_SORT && !pl.dense_out && !pl.order0 && p.nr > 0 && p.nnz >= 2 && npass >= 1 &&
+           npass <= 8 && p.d >= 2 && p.d <= 8;
+}
+
+static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Bytes of a batched problem's zeroed scratch: digit counts and look-back words.
+static size_t batch_zero_bytes(const Plan& pl) {
+    const int npass = plan_npass(pl);
+    return round256((size_t)npass * 256 * sizeof(uint32_t)) +
+           round256((size_t)npass * (size_t)sort_tiles(pl.desc.nnz) * 256 * sizeof(uint32_t));
+}
+
+// Plans, per-problem workspace offsets and the batched sort path's share:
+// its problems and its zeroed region [zero_off, zero_off + zero_bytes).
 static int batch_plans(const ttv_problem* probs, int32_t n, const ttv_opts* o, std::vector<Plan>& plans,
-                       std::vector<size_t>& ws_off, size_t& total) {
+                       std::vector<size_t>& ws_off, size_t& total, std::vector<int32_t>& batched,
+                       size_t& zero_off, size_t& zero_bytes) {
     plans.resize((size_t)n);
     ws_off.resize((size_t)n);
+    batched.clear();
     total = 0;
     for (int32_t i = 0; i < n; ++i) {
         const ttv_problem& q = probs[i];
         int rc = make_plan(&q.tensor, q.modes, q.n_v, q.vecs, q.v_dtype, nullptr, o, plans[(size_t)i]);
         if (rc != TTV_OK) return fail(rc, "problem %d: %s", i, g_err.c_str());
         ws_off[(size_t)i] = total;
-        total += (workspace_bytes(plans[(size_t)i]) + 255) & ~size_t(255);
+        total += round256(workspace_bytes(plans[(size_t)i]));
+        if (batch_sortable(plans[(size_t)i])) batched.push_back(i);
     }
+    zero_off = total;
+    zero_bytes = 0;
+    if (!batched.empty()) {
+        zero_bytes = 256;     // pass tickets
+        for (int32_t i : batched) zero_bytes += batch_zero_bytes(plans[(size_t)i]);
+    }
+    total += zero_bytes;
+    return TTV_OK;
+}
+
+// The launches of the batched problems' stages, with their job lists in
+// the entry's device table.
+struct BatchSortLaunch {
+    const BatchJob* jobs = nullptr;
+    struct Kt { JobList l; uint32_t units; int d; int lay; };
+    std::vector<Kt> kt;
+    JobList srt{};
+    int32_t count_per_pass[8] = {0};
+    uint32_t tiles_per_pass[8] = {0};
+    int max_npass = 0;
+    uint32_t* tickets = nullptr;
+    JobList rt[2]{}, rg[2]{};
+    uint32_t rtiles[2] = {0, 0}, rgroups[2] = {0, 0};
+    void* zero = nullptr;
+    size_t zero_bytes = 0;
+};
+
+// Builds the job table of the batched problems and uploads it (once, owned
+// by the entry; before the capture starts: the copy is synchronous).
+static int batch_sort_prepare(BatchEntry* e, const std::vector<Plan>& plans, const std::vector<size_t>& ws_off,
+                              const std::vector<int32_t>& batched, char* ws, size_t zero_off, size_t zero_bytes,
+                              ttv_out* outs, BatchSortLaunch& L) {
+    const size_t nb = batched.size();
+    char* zero = ws + zero_off;
+    uint32_t* tickets = reinterpret_cast<uint32_t*>(zero);
+    size_t zo = 256;
+    std::vector<BatchJob> jobs(nb);
+    for (size_t j = 0; j < nb; ++j) {
+        const int32_t i = batched[j];
+        const Plan& pl = plans[(size_t)i];
+        if (!outs[i].subs) return fail(TTV_ERR_ARG, "caller buffers need subs too (problem %d)", i);
+        Arena a;
+        a.base = ws + ws_off[(size_t)i];
+        WsPtrs w;
+        layout(pl, a, w);
+        BatchJob& J = jobs[j];
+        memset(&J, 0, sizeof J);
+        J.p = pl.desc;
+        Status* hs = g_status_pool.acquire();
+        if (!hs) return fail(TTV_ERR_NOMEM, "pinned status allocation failed");
+        e->status[(size_t)i] = hs;
+        memset(hs, 0, sizeof(Status));
+        void* dp = nullptr;
+        cudaError_t ce = cudaHostGetDevicePointer(&dp, hs, 0);
+        if (ce != cudaSuccess || !dp) return cuda_fail(ce, "status mapping");
+        J.p.status = static_cast<Status*>(dp);
+        for (int b = 0; b < 2; ++b) {
+            J.keys[b] = w.sb.keys[b];
+            J.vals[b] = w.sb.vals[b];
+        }
+        J.npass = plan_npass(pl);
+        J.ntiles = sort_tiles(pl.desc.nnz);
+        J.hist = reinterpret_cast<uint32_t*>(zero + zo);
+        zo += round256((size_t)J.npass * 256 * sizeof(uint32_t));
+        J.lookback = reinterpret_cast<uint32_t*>(zero + zo);
+        zo += round256((size_t)J.npass * (size_t)J.ntiles * 256 * sizeof(uint32_t));
+        J.rbk_state = w.rbk_state;
+        const int64_t cap = std::min(outs[i].subs_capacity, outs[i].vals_capacity);
+        J.o = SegOut{outs[i].subs, static_cast<double*>(outs[i].vals), cap, 0, pl.compensated};
+        ttv_out sh{};
+        sh.order = pl.desc.nr;
+        for (int m = 0; m < TTV_MAX_D; ++m) sh.shape[m] = m < pl.desc.nr ? pl.desc.rshape[m] : 0;
+        sh.dtype = TTV_F64;
+        e->shape[(size_t)i] = sh;
+        e->dense_out[(size_t)i] = 0;
+    }
+    if (zo != zero_bytes) return fail(TTV_ERR_CUDA, "batch scratch layout mismatch");
+
+    // job lists: one per (order, layout) for the key kernel; all jobs by
+    // decreasing pass count for the sort; one per accumulation for the reduction
+    struct HostList {
+        std::vector<int32_t> idx;
+        std::vector<uint32_t> prefix{0};
+        void add(int32_t j, uint64_t units) {
+            idx.push_back(j);
+            prefix.push_back(prefix.back() + (uint32_t)units);
+        }
+    };
+    std::vector<std::pair<int, HostList>> kt;          // key: d * 4 + layout class
+    HostList srt, rt[2], rg[2];
+    std::vector<int32_t> by_pass(nb);
+    for (size_t j = 0; j < nb; ++j) by_pass[j] = (int32_t)j;
+    std::stable_sort(by_pass.begin(), by_pass.end(), [&](int32_t a, int32_t b) { return jobs[a].npass > jobs[b].npass; });
+    for (int32_t j : by_pass) {
+        const BatchJob& J = jobs[(size_t)j];
+        const int key = J.p.d * 4 + keys_terms_batch_layout(J.p);
+        auto it = std::find_if(kt.begin(), kt.end(), [&](const std::pair<int, HostList>& c) { return c.first == key; });
+        if (it == kt.end()) {
+            kt.emplace_back(key, HostList{});
+            it = kt.end() - 1;
+        }
+        it->second.add(j, (uint64_t)((J.p.nnz + kKtBatchChunk - 1) / kKtBatchChunk));
+        srt.add(j, (uint64_t)J.ntiles);
+        const int c = J.o.compensated ? 1 : 0;
+        rt[c].add(j, (uint64_t)rbk_tiles(J.p.nnz));
+        rg[c].add(j, (uint64_t)rbk_groups(J.p.nnz));
+    }
+    for (size_t q = 0; q < nb; ++q) {
+        const BatchJob& J = jobs[(size_t)by_pass[q]];
+        L.max_npass = std::max(L.max_npass, (int)J.npass);
+        for (int p = 0; p < J.npass; ++p) {
+            L.count_per_pass[p] = (int32_t)q + 1;
+            L.tiles_per_pass[p] = srt.prefix[q + 1];
+        }
+    }
+    // one blob: the jobs, then every list's idx and prefix arrays
+    std::vector<char> blob;
+    auto put = [&](const void* src, size_t bytes) {
+        const size_t off = round256(blob.size());
+        blob.resize(off + bytes);
+        if (bytes) memcpy(blob.data() + off, src, bytes);
+        return off;
+    };
+    struct ListOff { size_t idx, prefix; int32_t count; };
+    auto put_list = [&](const HostList& l) {
+        ListOff r;
+        r.idx = put(l.idx.data(), l.idx.size() * sizeof(int32_t));
+        r.prefix = put(l.prefix.data(), l.prefix.size() * sizeof(uint32_t));
+        r.count = (int32_t)l.idx.size();
+        return r;
+    };
+    put(jobs.data(), nb * sizeof(BatchJob));
+    std::vector<ListOff> kt_off;
+    for (auto& c : kt) kt_off.push_back(put_list(c.second));
+    const ListOff srt_off = put_list(srt);
+    ListOff rt_off[2], rg_off[2];
+    for (int c = 0; c < 2; ++c) {
+        rt_off[c] = put_list(rt[c]);
+        rg_off[c] = put_list(rg[c]);
+    }
+    cudaError_t ce = cudaMalloc(&e->table, std::max<size_t>(blob.size(), 256));
+    if (ce != cudaSuccess) { e->table = nullptr; return cuda_fail(ce, "batch job table"); }
+    ce = cudaMemcpy(e->table, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) return cuda_fail(ce, "batch job table");
+    char* tb = static_cast<char*>(e->table);
+    auto dlist = [&](const ListOff& l) {
+        return JobList{reinterpret_cast<const int32_t*>(tb + l.idx), reinterpret_cast<const uint32_t*>(tb + l.prefix),
+                       l.count};
+    };
+    L.jobs = reinterpret_cast<const BatchJob*>(tb);
+    for (size_t c = 0; c < kt.size(); ++c)
+        L.kt.push_back(BatchSortLaunch::Kt{dlist(kt_off[c]), kt[c].second.prefix.back(), kt[c].first / 4,
+                                           kt[c].first % 4});
+    L.srt = dlist(srt_off);
+    L.tickets = tickets;
+    for (int c = 0; c < 2; ++c) {
+        L.rt[c] = dlist(rt_off[c]);
+        L.rg[c] = dlist(rg_off[c]);
+        L.rtiles[c] = rt[c].prefix.back();
+        L.rgroups[c] = rg[c].prefix.back();
+    }
+    L.zero = zero;
+    L.zero_bytes = zero_bytes;
+    e->batched = (int)nb;
+    return TTV_OK;
+}
+
+// The stages, in order, on one stream (being captured).
+static int batch_sort_issue(const BatchSortLaunch& L, cudaStream_t stream) {
+    cudaError_t ce = cudaMemsetAsync(L.zero, 0, L.zero_bytes, stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "batch scratch reset");
+    for (const BatchSortLaunch::Kt& k : L.kt) launch_keys_terms_batch(L.jobs, k.l, k.units, k.d, k.lay, stream);
+    launch_sort_batch(L.jobs, L.srt, L.count_per_pass, L.tiles_per_pass, L.max_npass, L.tickets, stream);
+    for (int c = 0; c < 2; ++c) launch_rbk_batch(L.jobs, L.rt[c], L.rtiles[c], L.rg[c], L.rgroups[c], c == 1, stream);
     return TTV_OK;
 }
 
@@ -1540,9 +1752,11 @@ static BatchEntry* batch_capture(const ttv_problem* probs, int32_t n, ttv_out* o
                                  uint64_t sig, int& rc) {
     std::vector<Plan> plans;
     std::vector<size_t> ws_off;
-    size_t total = 0;
-    rc = batch_plans(probs, n, o, plans, ws_off, total);
+    std::vector<int32_t> batched;
+    size_t total = 0, zero_off = 0, zero_bytes = 0;
+    rc = batch_plans(probs, n, o, plans, ws_off, total, batched, zero_off, zero_bytes);
     if (rc != TTV_OK) return nullptr;
+    if (o->path != TTV_PATH_AUTO && o->path != TTV_PATH_SORT) batched.clear();
     BatchEntry* e = new BatchEntry();
     e->sig = sig;
     char* ws = static_cast<char*>(o->workspace);
@@ -1568,6 +1782,16 @@ static BatchEntry* batch_capture(const ttv_problem* probs, int32_t n, ttv_out* o
     e->status.assign((size_t)n, nullptr);
     e->dense_out.assign((size_t)n, 0);
     e->shape.assign((size_t)n, ttv_out{});
+    BatchSortLaunch bl;
+    if (!batched.empty()) {
+        rc = batch_sort_prepare(e, plans, ws_off, batched, ws, zero_off, zero_bytes, outs, bl);
+        if (rc != TTV_OK) {
+            cudaEventDestroy(fork);
+            for (int k = 0; k < kBatchStreams; ++k) cudaEventDestroy(joins[k]);
+            destroy_entry(e);
+            return nullptr;
+        }
+    }
     t_capturing = 1;
     const long long before = prof_add_launches(0);
     cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
@@ -1576,15 +1800,23 @@ static BatchEntry* batch_capture(const ttv_problem* probs, int32_t n, ttv_out* o
     const int nstreams = std::min<int>(kBatchStreams, std::max<int32_t>(1, n));
     for (int k = 0; k < nstreams; ++k) cudaStreamWaitEvent(ss[k], fork, 0);
     rc = TTV_OK;
-    for (size_t j = 0; j < order.size(); ++j) {
+    // the batched problems' stages on the first stream, the rest dealt over the others
+    std::vector<char> on_batch((size_t)n, 0);
+    for (int32_t i : batched) on_batch[(size_t)i] = 1;
+    const int first_free = batched.empty() || nstreams == 1 ? 0 : 1;
+    if (!batched.empty()) rc = batch_sort_issue(bl, ss[0]);
+    size_t dealt = 0;
+    for (size_t j = 0; j < order.size() && rc == TTV_OK; ++j) {
         const int32_t i = order[j];
+        if (on_batch[(size_t)i]) continue;
         ttv_opts oi = *o;
         oi.async = 1;
         oi.workspace = ws + ws_off[(size_t)i];
         oi.workspace_bytes = workspace_bytes(plans[(size_t)i]);
         ttv_out tmp = outs[i];
         tmp.internal = nullptr;
-        const int r = execute(plans[(size_t)i], &tmp, &oi, ss[j % nstreams]);
+        const int r = execute(plans[(size_t)i], &tmp, &oi,
+                              ss[first_free + (int)(dealt++ % (size_t)(nstreams - first_free))]);
         OutState* st = static_cast<OutState*>(tmp.internal);
         if (st) {
             e->status[(size_t)i] = st->hstatus;
@@ -1630,8 +1862,9 @@ int ttv_batch_workspace_size(const ttv_problem* probs, int32_t n, const ttv_opts
     const ttv_opts* o = opts ? opts : &def;
     std::vector<Plan> plans;
     std::vector<size_t> off;
-    size_t total = 0;
-    int rc = batch_plans(probs, n, o, plans, off, total);
+    std::vector<int32_t> batched;
+    size_t total = 0, zero_off = 0, zero_bytes = 0;
+    int rc = batch_plans(probs, n, o, plans, off, total, batched, zero_off, zero_bytes);
     if (rc != TTV_OK) return rc;
     *bytes = total;
     return TTV_OK;

@@ -414,7 +414,7 @@ void launch_dense_fx(const StreamDesc& p, const FxPlan& fp, int want_presence, v
     f.part_hi = reinterpret_cast<long long*>(take((size_t)fp.grid * P * 8));
     f.part_L = reinterpret_cast<int*>(take((size_t)fp.grid * 4));
     f.pres_partials = want_presence ? reinterpret_cast<uint32_t*>(take((size_t)fp.grid * ((P + 31) / 32) * 4)) : nullptr;
-    cudaFuncSetAttribute(k_dense_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fp.smem_total);
+    smem_at_least(k_dense_fx, fp.smem_total);
     TTV_LAUNCH("dense_fx", stream, k_dense_fx<<<fp.grid, kFxThreads, fp.smem_total, stream>>>(f));
     const int64_t blocks = (P * 32 + 255) / 256;
     TTV_LAUNCH("dense_fx_reduce", stream,

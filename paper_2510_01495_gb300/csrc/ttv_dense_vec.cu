@@ -449,7 +449,7 @@ int dense_vec_grid(const StreamDesc& p, int want_presence) {
     const int mode = dense_vec_mode(p, want_presence);
     DenseVecKernel k = dense_vec_kernel(p.d, soa, dense_vec_products_int(p), mode);
     const size_t smem = dense_vec_smem(p, want_presence);
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+    smem_at_least(k, smem);
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kVecThreads, smem);
@@ -466,7 +466,7 @@ void launch_dense_vec(const StreamDesc& p, int want_presence, int G, double* par
         const bool intp = dense_vec_products_int(p) != 0;
         DenseTmaKernel k = dense_tma_kernel(p.d, soa, intp);
         const TmaLayout L = tma_layout(p, want_presence, intp);
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+        smem_at_least(k, L.total);
         TTV_LAUNCH("dense_accum", stream,
                    k<<<G, kTmaThreads, L.total, stream>>>(p, tma_chunk(p, G), want_presence, L, partials,
                                                           pres_partials));
@@ -479,7 +479,7 @@ void launch_dense_vec(const StreamDesc& p, int want_presence, int G, double* par
     vec_off = (vec_off + 15) & ~size_t(15);
     int64_t chunk = (p.nnz + G - 1) / G;
     chunk = (chunk + 1) & ~int64_t(1);
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+    smem_at_least(k, smem);
     TTV_LAUNCH("dense_accum", stream,
                k<<<G, kVecThreads, smem, stream>>>(p, chunk, want_presence, pres_off, vec_off, partials,
                                                    pres_partials));

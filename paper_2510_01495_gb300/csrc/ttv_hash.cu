@@ -125,7 +125,7 @@ static HashWs carve(const StreamDesc& p, const HashPlan& h, int dense_out, int k
     if (!h.direct && !dense_out) {
         const int npass = key_bits <= 0 ? 0 : (key_bits + 7) / 8;
         const int64_t n = h.bound;
-        const int64_t ntiles = (n + 4095) / 4096;
+        const int64_t ntiles = sort_tiles(n);
         w.sb.keys[0] = reinterpret_cast<uint64_t*>(take((size_t)n * 8));
         w.sb.keys[1] = reinterpret_cast<uint64_t*>(take((size_t)n * 8));
         w.sb.vals[0] = reinterpret_cast<double*>(take((size_t)n * 8));
@@ -459,7 +459,7 @@ void launch_hash(const StreamDesc& p, int dense_out, int key_bits, void* ws, int
     const int unroll = p.items == 4 ? 4 : 2;
     auto kins = h.direct ? (unroll == 2 ? k_hash_insert<true, 2> : k_hash_insert<true, 4>)
                          : (unroll == 2 ? k_hash_insert<false, 2> : k_hash_insert<false, 4>);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kins, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_at_least(kins, smem);
     const int64_t want = (p.nnz + kHashThreads * unroll - 1) / (kHashThreads * unroll);
     const int per_sm = p.ctas_per_sm > 0 ? p.ctas_per_sm : 8;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * per_sm));

@@ -328,6 +328,15 @@ __device__ __forceinline__ bool spin_until(const volatile uint32_t* addr, uint32
 // ---- launch bookkeeping (ttv_prof.cu) --------------------------------------
 void prof_begin(const char* name, cudaStream_t s);
 void prof_end(cudaStream_t s);
+
+// Raises a kernel's dynamic shared memory limit to at least `bytes`, never
+// lowering it: a lower limit set for one problem would make launches (and
+// captured graph nodes) sized for another fail.  Thread-safe.
+void smem_limit_at_least(const void* kernel, size_t bytes);
+template <class K>
+inline void smem_at_least(K* kernel, size_t bytes) {
+    smem_limit_at_least(reinterpret_cast<const void*>(kernel), bytes);
+}
 // Every kernel launch goes through this: counted, and timed when profiling.
 #define TTV_LAUNCH(name, stream, ...)      \
     do {                                   \
@@ -386,6 +395,46 @@ struct PrepTerms {
     const int32_t* sub[kMaxD];
     const void* vec[kMaxD];
 };
+// One problem of a batch on the sort path run stage-wise: every stage
+// (keys and terms, histogram scan, each digit pass, the reduce-by-key
+// stages) is one launch over all problems of the batch, each CTA finding its
+// problem and its tile by a binary search over per-problem unit counts.
+struct BatchJob {
+    StreamDesc p;               // p.status: the problem's status block
+    uint64_t* keys[2];          // pair buffers (nnz each, 16-byte aligned)
+    double* vals[2];
+    uint32_t* hist;             // npass x 256 digit counts, zeroed before the batch
+    uint32_t* lookback;         // npass x ntiles x 256 look-back words, zeroed before the batch
+    void* rbk_state;            // rbk_state_bytes(nnz)
+    SegOut o;                   // sparse result rows
+    int64_t ntiles;             // radix-sort tiles
+    int32_t npass;              // 8-bit digit passes (1..8)
+    int32_t pad;
+};
+
+// The problems one batched stage covers: idx[0..count) in the order of
+// prefix, prefix[j] = units (CTAs or warps) before problem idx[j],
+// prefix[count] = the total.
+struct JobList {
+    const int32_t* idx;
+    const uint32_t* prefix;
+    int32_t count;
+};
+
+constexpr int64_t kKtBatchChunk = 16384;   // nonzeros per CTA of the batched key kernel
+int64_t sort_tiles(int64_t n);             // radix-sort tiles of n pairs
+int64_t rbk_tiles(int64_t n);              // reduce-by-key tiles of n pairs
+int64_t rbk_groups(int64_t n);             // reduce-by-key tile groups of n pairs
+
+// The stages over a batch; every job list is in device memory.
+int keys_terms_batch_layout(const StreamDesc& p);
+void launch_keys_terms_batch(const BatchJob* jobs, const JobList& l, uint32_t units, int d, int lay,
+                             cudaStream_t stream);
+void launch_sort_batch(const BatchJob* jobs, const JobList& all, const int32_t* count_per_pass,
+                       const uint32_t* tiles_per_pass, int max_npass, uint32_t* tickets, cudaStream_t stream);
+void launch_rbk_batch(const BatchJob* jobs, const JobList& tiles, uint32_t ntiles, const JobList& groups,
+                      uint32_t ngroup_warps, bool compensated, cudaStream_t stream);
+
 // Sorts (keys, vals) stably by the low `bits` bits of the key; returns which
 // buffer (0/1) holds the result.  With n_dev, the pair count is
 // min(n, *n_dev), read on the device (n is then the upper bound the buffers

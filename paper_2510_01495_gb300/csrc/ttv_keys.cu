@@ -37,26 +37,31 @@ __device__ __forceinline__ bool kt_item(const StreamDesc& p, const double* sv, c
     return good;
 }
 
-template <int D, bool kSoA>
-__global__ void __launch_bounds__(kKtThreads) k_keys_terms_vec(StreamDesc p, uint64_t* __restrict__ keys,
-                                                               double* __restrict__ terms, int npass,
-                                                               uint32_t* __restrict__ hist) {
-    extern __shared__ double sv[];
-    __shared__ uint32_t sh[kKtMaxPass * 256];
-    for (int i = threadIdx.x; i < npass * 256; i += kKtThreads) sh[i] = 0;
-    stage_vectors(p, sv);
-    __syncthreads();
+// Pairs q0 + threadIdx.x, + stride, ... below q1 (pair q: nonzeros 2q and
+// 2q + 1), the odd last nonzero too when `tail`; digit counts into sh.
+// Subscript layouts: AoS rows, SoA columns with an even stride (16-byte
+// column-pair loads), or any strides (one 8-byte load per subscript).
+enum { kLayAoS = 0, kLaySoA = 1, kLayAny = 2 };
+
+template <int D, int kLay>
+__device__ __forceinline__ void kt_range(const StreamDesc& p, const double* sv, uint64_t* __restrict__ keys,
+                                         double* __restrict__ terms, int npass, uint32_t* sh, int64_t q0,
+                                         int64_t q1, int64_t stride, bool tail) {
     const double* vd = static_cast<const double*>(p.vals);
     const float* vf = static_cast<const float*>(p.vals);
-    const int64_t npairs = p.nnz / 2;
-    const int64_t stride = (int64_t)gridDim.x * kKtThreads;
     auto count = [&](uint64_t key) {
         for (int q = 0; q < npass; ++q) atomicAdd(&sh[q * 256 + ((key >> (8 * q)) & 255u)], 1u);
     };
-    for (int64_t q = (int64_t)blockIdx.x * kKtThreads + threadIdx.x; q < npairs; q += stride) {
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += stride) {
         const int64_t k = 2 * q;
         int64_t s0[D], s1[D];
-        if constexpr (kSoA) {
+        if constexpr (kLay == kLayAny) {
+#pragma unroll
+            for (int m = 0; m < D; ++m) {
+                s0[m] = __ldcs(p.subs + k * p.snz + m * p.smode);
+                s1[m] = __ldcs(p.subs + (k + 1) * p.snz + m * p.smode);
+            }
+        } else if constexpr (kLay == kLaySoA) {
 #pragma unroll
             for (int m = 0; m < D; ++m) {
                 const longlong2 w = __ldcs(reinterpret_cast<const longlong2*>(p.subs + m * p.smode + k));
@@ -74,7 +79,10 @@ __global__ void __launch_bounds__(kKtThreads) k_keys_terms_vec(StreamDesc p, uin
             }
         }
         double v0, v1;
-        if (p.val_f32) {
+        if (kLay == kLayAny) {
+            v0 = p.val_f32 ? (double)__ldcs(vf + k) : __ldcs(vd + k);
+            v1 = p.val_f32 ? (double)__ldcs(vf + k + 1) : __ldcs(vd + k + 1);
+        } else if (p.val_f32) {
             const float2 w = __ldcs(reinterpret_cast<const float2*>(vf + k));
             v0 = (double)w.x;
             v1 = (double)w.y;
@@ -98,7 +106,7 @@ __global__ void __launch_bounds__(kKtThreads) k_keys_terms_vec(StreamDesc p, uin
         count(k1);
     }
     // odd tail
-    if ((p.nnz & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    if ((p.nnz & 1) && tail && threadIdx.x == 0) {
         const int64_t k = p.nnz - 1;
         int64_t s0[D];
 #pragma unroll
@@ -115,9 +123,60 @@ __global__ void __launch_bounds__(kKtThreads) k_keys_terms_vec(StreamDesc p, uin
         terms[k] = t0;
         count(k0);
     }
+}
+
+template <int D, bool kSoA>
+__global__ void __launch_bounds__(kKtThreads) k_keys_terms_vec(StreamDesc p, uint64_t* __restrict__ keys,
+                                                               double* __restrict__ terms, int npass,
+                                                               uint32_t* __restrict__ hist) {
+    extern __shared__ double sv[];
+    __shared__ uint32_t sh[kKtMaxPass * 256];
+    for (int i = threadIdx.x; i < npass * 256; i += kKtThreads) sh[i] = 0;
+    stage_vectors(p, sv);
+    __syncthreads();
+    kt_range<D, kSoA ? kLaySoA : kLayAoS>(p, sv, keys, terms, npass, sh, (int64_t)blockIdx.x * kKtThreads, p.nnz / 2,
+                      (int64_t)gridDim.x * kKtThreads, blockIdx.x == 0);
     __syncthreads();
     for (int i = threadIdx.x; i < npass * 256; i += kKtThreads)
         if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// Batched form: CTA c takes chunk c - prefix[j] (kKtBatchChunk nonzeros) of
+// problem idx[j]; vectors are gathered from global memory (L2) rather than
+// staged, a chunk being too short to repay staging a whole vector.
+template <int D, int kLay>
+__global__ void __launch_bounds__(kKtThreads) k_keys_terms_batch(const BatchJob* __restrict__ jobs, JobList l) {
+    __shared__ uint32_t sh[kKtMaxPass * 256];
+    __shared__ __align__(16) StreamDesc sp;
+    __shared__ int s_pos;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = l.count;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(l.prefix + mid) <= blockIdx.x) lo = mid;
+            else hi = mid;
+        }
+        s_pos = lo;
+    }
+    __syncthreads();
+    const int pos = s_pos;
+    const BatchJob& J = jobs[__ldg(l.idx + pos)];
+    static_assert(sizeof(StreamDesc) % 8 == 0, "descriptor copied in 8-byte words");
+    for (int i = threadIdx.x; i < (int)(sizeof(StreamDesc) / 8); i += kKtThreads)
+        reinterpret_cast<uint64_t*>(&sp)[i] = reinterpret_cast<const uint64_t*>(&J.p)[i];
+    const int npass = J.npass;
+    for (int i = threadIdx.x; i < npass * 256; i += kKtThreads) sh[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) sp.vec_smem = 0;
+    __syncthreads();
+    const int64_t chunk = (int64_t)blockIdx.x - __ldg(l.prefix + pos);
+    const int64_t nchunks = (sp.nnz + kKtBatchChunk - 1) / kKtBatchChunk;
+    const int64_t q0 = chunk * (kKtBatchChunk / 2);
+    const int64_t q1 = min(sp.nnz / 2, q0 + kKtBatchChunk / 2);
+    kt_range<D, kLay>(sp, nullptr, J.keys[0], J.vals[0], npass, sh, q0, q1, kKtThreads, chunk == nchunks - 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * 256; i += kKtThreads)
+        if (sh[i]) atomicAdd(&J.hist[i], sh[i]);
 }
 
 typedef void (*KtKernel)(StreamDesc, uint64_t*, double*, int, uint32_t*);
@@ -158,11 +217,49 @@ void launch_keys_terms_vec(const StreamDesc& p, uint64_t* keys, double* terms, i
     if (p.nnz <= 0) return;
     KtKernel k = kt_kernel(p.d, p.snz == 1);
     const size_t smem = p.vec_smem ? (size_t)p.vtotal * sizeof(double) : 0;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+    smem_at_least(k, smem);
     const int per_sm = p.ctas_per_sm > 0 ? p.ctas_per_sm : 8;
     const int64_t want = (p.nnz / 2 + kKtThreads - 1) / kKtThreads;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * per_sm));
     TTV_LAUNCH("keys_terms", stream, k<<<grid, kKtThreads, smem, stream>>>(p, keys, terms, npass, hist));
+}
+
+typedef void (*KtBatchKernel)(const BatchJob*, JobList);
+
+template <int D>
+static KtBatchKernel ktb_pick(int lay) {
+    return lay == kLayAoS ? k_keys_terms_batch<D, kLayAoS>
+                          : lay == kLaySoA ? k_keys_terms_batch<D, kLaySoA> : k_keys_terms_batch<D, kLayAny>;
+}
+
+// The batched key kernel's layout class of a problem: 0 AoS rows, 1 SoA
+// columns with an even stride (both with 16-byte aligned subscripts and
+// values), 2 anything else.
+int keys_terms_batch_layout(const StreamDesc& p) {
+    const uintptr_t sb = reinterpret_cast<uintptr_t>(p.subs), vb = reinterpret_cast<uintptr_t>(p.vals);
+    const bool aligned = !(sb & 15) && !(vb & 15);
+    if (aligned && p.snz == p.d && p.smode == 1) return kLayAoS;
+    if (aligned && p.snz == 1 && p.smode % 2 == 0) return kLaySoA;
+    return kLayAny;
+}
+
+// Keys, terms and digit counts of every problem in l (all of order d and
+// layout class lay); units = total chunks.
+void launch_keys_terms_batch(const BatchJob* jobs, const JobList& l, uint32_t units, int d, int lay,
+                             cudaStream_t stream) {
+    if (l.count <= 0 || units == 0) return;
+    KtBatchKernel k = nullptr;
+    switch (d) {
+        case 2: k = ktb_pick<2>(lay); break;
+        case 3: k = ktb_pick<3>(lay); break;
+        case 4: k = ktb_pick<4>(lay); break;
+        case 5: k = ktb_pick<5>(lay); break;
+        case 6: k = ktb_pick<6>(lay); break;
+        case 7: k = ktb_pick<7>(lay); break;
+        case 8: k = ktb_pick<8>(lay); break;
+        default: return;
+    }
+    TTV_LAUNCH("keys_terms_batch", stream, k<<<units, kKtThreads, 0, stream>>>(jobs, l));
 }
 
 }  // namespace ttv

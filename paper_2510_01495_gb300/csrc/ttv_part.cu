@@ -139,7 +139,7 @@ static Carve part_layout(char* base, int64_t nnz, int key_bits, PartWs& w, int h
     // than the row-major key space: room for the widest (eight passes)
     (void)key_bits;
     const int npass = 8;
-    const int64_t ntiles = (S + 4095) / 4096;
+    const int64_t ntiles = sort_tiles(S);
     w.sb.keys[0] = a.take<uint64_t>(S);
     w.sb.keys[1] = a.take<uint64_t>(S);
     w.sb.vals[0] = a.take<double>(S);

@@ -27,6 +27,21 @@ static std::map<std::string, std::pair<double, long long>> g_totals;
 static thread_local Pending t_open{nullptr, nullptr, nullptr};
 thread_local int t_capturing = 0;     // inside a graph capture: count, never record events
 
+void smem_limit_at_least(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;   // (device, kernel) -> bytes set
+    if (bytes <= 48 * 1024) return;      // the default limit
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    size_t& cur = limit[{dev, kernel}];
+    if (bytes <= cur) return;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+        cur = bytes;
+    else
+        cudaGetLastError();   // the launch reports the error
+}
+
 long long prof_add_launches(long long n) { return g_launches.fetch_add(n) + n; }
 
 static cudaEvent_t get_event() {

@@ -22,14 +22,19 @@ namespace ttv {
 
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
+// A digit pass takes 4096-pair tiles with 256 threads of 16 pairs, three
+// CTAs per SM (measured against 512 threads of 8 pairs at two CTAs per SM:
+// 8.60 against 8.91 ms for the 1e8-nonzero Zipf TTV).
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;      // 4096 keys per tile
+constexpr int kScanWarps = 8;                              // warps of the 256-thread scans
 constexpr int kHistStride = kRadix + 1;                    // +1: padding bucket for absent items
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
+constexpr int kLookWindow = 8;          // predecessor tiles read per look-back round trip
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
     uint32_t v;
@@ -58,7 +63,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_
     __syncthreads();
     uint32_t before = 0, all = 0;
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
+    for (int w = 0; w < kScanWarps; ++w) {
         uint32_t t = warp_tot[w];
         if (w < warp) before += t;
         all += t;
@@ -89,7 +94,7 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint64_t* __restrict__
 
 // In place: hist[p][d] -> exclusive prefix over digits of pass p.
 __global__ void __launch_bounds__(256) k_radix_hist_scan(uint32_t* hist, int npass) {
-    __shared__ uint32_t wt[kSortWarps];
+    __shared__ uint32_t wt[kScanWarps];
     for (int p = 0; p < npass; ++p) {
         uint32_t x = hist[p * kRadix + threadIdx.x];
         uint32_t total;
@@ -104,7 +109,7 @@ __global__ void __launch_bounds__(256) k_radix_hist_scan(uint32_t* hist, int npa
 struct OnesweepSmem {
     uint32_t whist[kSortWarps * kHistStride];
     uint32_t tile_start[kRadix];
-    uint32_t gbase[kRadix];
+    uint32_t gdelta[kRadix];         // output index of tile slot j: gdelta[digit] + j
     uint32_t warp_tot[kSortWarps];
     uint32_t tile;
     uint32_t pad[3];
@@ -112,31 +117,41 @@ struct OnesweepSmem {
     double vals[kSortTile];
 };
 
-__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const uint64_t* __restrict__ keys_in,
-                                                           const double* __restrict__ vals_in,
-                                                           uint64_t* __restrict__ keys_out,
-                                                           double* __restrict__ vals_out, int64_t n, int shift,
-                                                           const uint32_t* __restrict__ digit_off,
-                                                           uint32_t* lookback, uint32_t* ticket, Status* st,
-                                                           const unsigned long long* __restrict__ n_dev) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    OnesweepSmem& sm = *reinterpret_cast<OnesweepSmem*>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-    if (tid == 0) sm.tile = atomicAdd(ticket, 1u);
-    for (int i = tid; i < kSortWarps * kHistStride; i += kSortThreads) sm.whist[i] = 0;
+// Exclusive scan of the digit counts held by threads [0, kRadix) of a
+// kSortThreads block; the other threads only pass through the barriers.
+__device__ __forceinline__ uint32_t digit_exclusive_scan(uint32_t x, uint32_t* warp_tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31 && warp < kRadix / 32) warp_tot[warp] = inc;
     __syncthreads();
-    const uint32_t tile = sm.tile;
+    uint32_t before = 0;
+#pragma unroll
+    for (int w = 0; w < kRadix / 32; ++w)
+        if (w < warp) before += warp_tot[w];
+    return before + inc - x;
+}
+
+// The pass over one tile, once the CTA holds its ticket and its warp
+// histograms are zero (called by the single-problem and the batched kernel).
+__device__ __forceinline__ void onesweep_tile(OnesweepSmem& sm, const uint64_t* __restrict__ keys_in,
+                                              const double* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
+                                              double* __restrict__ vals_out, int64_t n, int shift,
+                                              const uint32_t* __restrict__ digit_off, uint32_t* lookback,
+                                              Status* st, uint32_t tile) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = (int64_t)tile * kSortTile;
-    // With the count on the device, tiles past it have nothing to do; no
-    // tile with work waits on them (look-back only reads earlier tiles).
-    if (n_dev) n = min(n, (int64_t)*n_dev);
     if (base >= n) return;
+    const bool digit_thread = tid < kRadix;        // thread t < 256 owns digit t
+    const uint32_t doff = digit_thread ? __ldg(digit_off + tid) : 0u;   // needed after the look-back
 
     // Keys first: ranking needs only them, and they go to shared memory
-    // before the values are loaded, so that at most 16 keys or 16 values
-    // (plus one packed word per item) are live per thread and three CTAs fit
-    // on an SM.
+    // before the values are loaded, so that at most 8 keys or 8 values (plus
+    // one packed word per item) are live per thread.
     uint64_t k[kSortItems];
     uint32_t rd[kSortItems];     // rank << 9 | digit, then the staging slot
     const int64_t wbase = base + warp * (kSortItems * 32) + lane;
@@ -145,14 +160,23 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const uint64_t* __
         const int64_t idx = wbase + i * 32;
         k[i] = idx < n ? __ldcs(keys_in + idx) : 0ull;
     }
-    // Warp-level multi-split: rank of each item among equal digits of its warp.
+    // Warp-level multi-split: rank of each item among equal digits of its
+    // warp.  The lanes holding the same digit are found by one ballot per
+    // digit bit (nine: the digit and the padding bucket), measured faster
+    // than __match_any_sync here.
     uint32_t* wh = sm.whist + warp * kHistStride;
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
         // padding bucket kRadix for absent items: never published or written
         const uint32_t dig = wbase + i * 32 < n ? (uint32_t)(k[i] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
-        const uint32_t mask = __match_any_sync(0xffffffffu, dig);
+        uint32_t mask = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b <= kRadixBits; ++b) {
+            const uint32_t bit = (dig >> b) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+            mask &= bit ? bal : ~bal;
+        }
         const int leader = __ffs(mask) - 1;
         uint32_t b = 0;
         if (lane == leader) {
@@ -167,14 +191,16 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const uint64_t* __
 
     // Thread t owns digit t: prefix over warps, tile count, tile-local start.
     uint32_t cnt = 0;
+    if (digit_thread) {
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-        const uint32_t c = sm.whist[w * kHistStride + tid];
-        sm.whist[w * kHistStride + tid] = cnt;
-        cnt += c;
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = sm.whist[w * kHistStride + tid];
+            sm.whist[w * kHistStride + tid] = cnt;
+            cnt += c;
+        }
     }
-    uint32_t tile_total;
-    sm.tile_start[tid] = block_exclusive_scan_256(cnt, sm.warp_tot, tile_total);
+    const uint32_t start = digit_exclusive_scan(cnt, sm.warp_tot);
+    if (digit_thread) sm.tile_start[tid] = start;
     __syncthreads();
 
     // Keys into shared memory in digit order (stable); keep each item's slot.
@@ -198,32 +224,47 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const uint64_t* __
         v[i] = idx < n ? __ldcs(vals_in + idx) : 0.0;
     }
 
-    // Decoupled look-back across tiles for digit t.
+    // Decoupled look-back across tiles for digit t.  The words of up to
+    // kLookWindow predecessors are loaded together (one L2 round trip for
+    // the window rather than one per tile), then taken in order; a word not
+    // yet published is polled on its own.
     uint32_t* my = lookback + (size_t)tile * kRadix + tid;
     uint32_t exclusive = 0;
-    if (tile == 0) {
+    if (!digit_thread) {
+    } else if (tile == 0) {
         st_relaxed(my, kFlagInc | cnt);
     } else {
         st_relaxed(my, kFlagAgg | cnt);
         int64_t j = (int64_t)tile - 1;
         const uint32_t polls = wait_limit(1u << 24);
-        while (j >= 0) {
-            const uint32_t* q = lookback + (size_t)j * kRadix + tid;
-            uint32_t val = 0;
-            bool ok = false;
-            for (uint32_t it = 0; it < polls; ++it) {
-                val = ld_relaxed(q);
-                if (val & (kFlagAgg | kFlagInc)) { ok = true; break; }
-                if (it > 32) __nanosleep(32);
+        bool done = false;
+        while (!done && j >= 0) {
+            uint32_t w[kLookWindow];
+#pragma unroll
+            for (int u = 0; u < kLookWindow; ++u)
+                w[u] = j - u >= 0 ? ld_relaxed(lookback + (size_t)(j - u) * kRadix + tid) : 0u;
+#pragma unroll
+            for (int u = 0; u < kLookWindow; ++u) {
+                if (done || j - u < 0) { done = true; break; }
+                uint32_t val = w[u];
+                if (!(val & (kFlagAgg | kFlagInc))) {
+                    const uint32_t* q = lookback + (size_t)(j - u) * kRadix + tid;
+                    bool ok = false;
+                    for (uint32_t it = 0; it < polls; ++it) {
+                        val = ld_relaxed(q);
+                        if (val & (kFlagAgg | kFlagInc)) { ok = true; break; }
+                        if (it > 32) __nanosleep(32);
+                    }
+                    if (!ok) { set_error(st, kErrTimeout); done = true; break; }
+                }
+                exclusive += val & kCountMask;
+                if (val & kFlagInc) done = true;
             }
-            if (!ok) { set_error(st, kErrTimeout); break; }
-            exclusive += val & kCountMask;
-            if (val & kFlagInc) break;
-            --j;
+            j -= kLookWindow;
         }
         st_relaxed(my, kFlagInc | ((exclusive + cnt) & kCountMask));
     }
-    sm.gbase[tid] = digit_off[tid] + exclusive;
+    if (digit_thread) sm.gdelta[tid] = doff + exclusive - start;
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i)
         if (rd[i] != kAbsent) sm.vals[rd[i]] = v[i];
@@ -234,10 +275,107 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const uint64_t* __
     for (int j = tid; j < tile_n; j += kSortThreads) {
         const uint64_t kk = sm.keys[j];
         const uint32_t d = (uint32_t)(kk >> shift) & (kRadix - 1);
-        const uint32_t out = sm.gbase[d] + (uint32_t)j - sm.tile_start[d];
+        const uint32_t out = sm.gdelta[d] + (uint32_t)j;
         if ((int64_t)out >= n) continue;     // only after a look-back ran out: offsets are then unreliable
         keys_out[out] = kk;
         vals_out[out] = sm.vals[j];
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const uint64_t* __restrict__ keys_in,
+                                                           const double* __restrict__ vals_in,
+                                                           uint64_t* __restrict__ keys_out,
+                                                           double* __restrict__ vals_out, int64_t n, int shift,
+                                                           const uint32_t* __restrict__ digit_off,
+                                                           uint32_t* lookback, uint32_t* ticket, Status* st,
+                                                           const unsigned long long* __restrict__ n_dev) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    OnesweepSmem& sm = *reinterpret_cast<OnesweepSmem*>(smem_raw);
+    const int tid = threadIdx.x;
+    if (tid == 0) sm.tile = atomicAdd(ticket, 1u);
+    for (int i = tid; i < kSortWarps * kHistStride; i += kSortThreads) sm.whist[i] = 0;
+    __syncthreads();
+    const uint32_t tile = sm.tile;
+    // With the count on the device, tiles past it have nothing to do; no
+    // tile with work waits on them (look-back only reads earlier tiles).
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    onesweep_tile(sm, keys_in, vals_in, keys_out, vals_out, n, shift, digit_off, lookback, st, tile);
+}
+
+// The position in a job list of the problem that unit t falls in:
+// prefix[j] <= t < prefix[j + 1] (problems with no units are skipped).
+__device__ __forceinline__ int job_of(const uint32_t* __restrict__ prefix, int count, uint32_t t) {
+    int lo = 0, hi = count;          // prefix[lo] <= t < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// One digit pass over the tiles of every problem of a batch with more than
+// `pass` digits (the list's first l.count problems).  CTAs take global
+// tickets, problem after problem, so each problem's tiles are claimed in
+// increasing order and its look-back only waits on tiles claimed before.
+__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_batch(const BatchJob* __restrict__ jobs, JobList l,
+                                                                 int pass, uint32_t* ticket) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    OnesweepSmem& sm = *reinterpret_cast<OnesweepSmem*>(smem_raw);
+    __shared__ int s_pos;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        const uint32_t t = atomicAdd(ticket, 1u);
+        sm.tile = t;
+        s_pos = t < __ldg(l.prefix + l.count) ? job_of(l.prefix, l.count, t) : -1;
+    }
+    for (int i = tid; i < kSortWarps * kHistStride; i += kSortThreads) sm.whist[i] = 0;
+    __syncthreads();
+    const int pos = s_pos;
+    if (pos < 0) return;
+    const BatchJob& J = jobs[__ldg(l.idx + pos)];
+    const int cur = pass & 1;
+    onesweep_tile(sm, J.keys[cur], J.vals[cur], J.keys[cur ^ 1], J.vals[cur ^ 1], J.p.nnz, pass * kRadixBits,
+                  J.hist + pass * kRadix, J.lookback + (size_t)pass * J.ntiles * kRadix, J.p.status,
+                  sm.tile - __ldg(l.prefix + pos));
+}
+
+// Each problem's digit counts into exclusive prefixes: one CTA per problem.
+__global__ void __launch_bounds__(256) k_radix_hist_scan_batch(const BatchJob* __restrict__ jobs, JobList l) {
+    __shared__ uint32_t wt[kScanWarps];
+    const BatchJob& J = jobs[__ldg(l.idx + blockIdx.x)];
+    for (int p = 0; p < J.npass; ++p) {
+        uint32_t x = J.hist[p * kRadix + threadIdx.x];
+        uint32_t total;
+        uint32_t ex = block_exclusive_scan_256(x, wt, total);
+        J.hist[p * kRadix + threadIdx.x] = ex;
+        __syncthreads();
+    }
+}
+
+int64_t sort_tiles(int64_t n) { return (std::max<int64_t>(n, 1) + kSortTile - 1) / kSortTile; }
+
+// Digit passes of a batch: the list is ordered by decreasing pass count, so
+// pass p covers its first count_per_pass[p] problems (tiles_per_pass[p]
+// tiles); tickets: one zeroed counter per pass.
+void launch_sort_batch(const BatchJob* jobs, const JobList& all, const int32_t* count_per_pass,
+                       const uint32_t* tiles_per_pass, int max_npass, uint32_t* tickets, cudaStream_t stream) {
+    if (all.count <= 0 || max_npass <= 0) return;
+    TTV_LAUNCH("radix_hist_scan", stream, k_radix_hist_scan_batch<<<(unsigned)all.count, 256, 0, stream>>>(jobs, all));
+    const size_t smem = sizeof(OnesweepSmem);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_onesweep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_onesweep_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        attr_set = true;
+    }
+    for (int p = 0; p < max_npass; ++p) {
+        if (count_per_pass[p] <= 0 || tiles_per_pass[p] == 0) break;
+        JobList lp = all;
+        lp.count = count_per_pass[p];
+        TTV_LAUNCH("onesweep_batch", stream,
+                   k_onesweep_batch<<<tiles_per_pass[p], kSortThreads, smem, stream>>>(jobs, lp, p, tickets + p));
     }
 }
 
@@ -668,13 +806,14 @@ __device__ __forceinline__ void rbk_block_scan(const RbkPairs& r, RbkScanSmem& s
 // last head and the threads after it form and add terms.  The partial sums
 // are combined in a fixed order (shuffle tree, then warps left to right).
 template <bool kComp, class H, class Src>
-__global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles(H hd, Src src, int64_t n, RbkSum* __restrict__ tiles) {
+__device__ __forceinline__ void rbk_tiles_body(const H& hd, const Src& src, int64_t n, int64_t tile,
+                                               RbkSum* __restrict__ out) {
     __shared__ int s_last[kRbkThreads / 32];
     __shared__ uint32_t s_cnt[kRbkThreads / 32];
     __shared__ double s_val[kRbkThreads / 32];
     __shared__ double s_k[kRbkThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t g0 = (int64_t)blockIdx.x * kRbkTile + (int64_t)tid * kRbkItems;
+    const int64_t g0 = tile * kRbkTile + (int64_t)tid * kRbkItems;
     const int nmine = (int)max((int64_t)0, min((int64_t)kRbkItems, n - g0));
     const uint32_t heads = rbk_heads(hd, n, g0, nmine);
     // last thread with a head (-1: none) and the head count
@@ -733,21 +872,24 @@ __global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles(H hd, Src src, int64_
         t.comp = vk;
         t.cnt = cnt;
         t.flag = last >= 0;
-        tiles[blockIdx.x] = t;
+        *out = t;
     }
+}
+
+template <bool kComp, class H, class Src>
+__global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles(H hd, Src src, int64_t n, RbkSum* __restrict__ tiles) {
+    rbk_tiles_body<kComp>(hd, src, n, blockIdx.x, tiles + blockIdx.x);
 }
 
 // One warp per group of 32 tiles: each tile's exclusive prefix within the
 // group (ingroup[t]) and the group's summary (groups[g]).
 constexpr int kRbkGroup = 32;
 
+// Group g of a problem's tiles, by one whole warp.
 template <bool kComp>
-__global__ void __launch_bounds__(256) k_rbk_groups(const RbkSum* __restrict__ tiles, int64_t ntiles,
-                                                    RbkSum* __restrict__ ingroup, RbkSum* __restrict__ groups,
-                                                    int64_t ngroups) {
-    const int lane = threadIdx.x & 31;
-    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (g >= ngroups) return;
+__device__ __forceinline__ void rbk_group_body(const RbkSum* __restrict__ tiles, int64_t ntiles,
+                                               RbkSum* __restrict__ ingroup, RbkSum* __restrict__ groups,
+                                               int64_t g, int lane) {
     const int64_t t = g * kRbkGroup + lane;
     RbkSum a = t < ntiles ? tiles[t] : RbkSum{0.0, 0.0, 0u, 0u};
     uint32_t c = a.cnt, f = a.flag;
@@ -769,6 +911,15 @@ __global__ void __launch_bounds__(256) k_rbk_groups(const RbkSum* __restrict__ t
     if (lane == 31) groups[g] = RbkSum{v, k, c, f};
 }
 
+template <bool kComp>
+__global__ void __launch_bounds__(256) k_rbk_groups(const RbkSum* __restrict__ tiles, int64_t ntiles,
+                                                    RbkSum* __restrict__ ingroup, RbkSum* __restrict__ groups,
+                                                    int64_t ngroups) {
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= ngroups) return;
+    rbk_group_body<kComp>(tiles, ntiles, ingroup, groups, g, threadIdx.x & 31);
+}
+
 // Exclusive scan of the group summaries; gprefix[g] = open value entering
 // group g, gheads[g] = heads before it; the total head count is the result
 // size.
@@ -787,10 +938,9 @@ __device__ __forceinline__ void cat_sum(double va, double ka, double& vb, double
 }
 
 template <bool kComp>
-__global__ void __launch_bounds__(kRbkScanThreads) k_rbk_scan(const RbkSum* __restrict__ groups, int64_t ngroups,
-                                                              RbkSum* __restrict__ gprefix,
-                                                              unsigned long long* __restrict__ gheads,
-                                                              Status* st) {
+__device__ __forceinline__ void rbk_scan_body(const RbkSum* __restrict__ groups, int64_t ngroups,
+                                              RbkSum* __restrict__ gprefix, unsigned long long* __restrict__ gheads,
+                                              Status* st) {
     __shared__ uint32_t s_flag[kRbkScanThreads / 32];
     __shared__ double s_val[kRbkScanThreads / 32];
     __shared__ double s_k[kRbkScanThreads / 32];
@@ -880,6 +1030,14 @@ __global__ void __launch_bounds__(kRbkScanThreads) k_rbk_scan(const RbkSum* __re
     if (hi == ngroups && lo < hi) st->nnz_out = rc;
 }
 
+template <bool kComp>
+__global__ void __launch_bounds__(kRbkScanThreads) k_rbk_scan(const RbkSum* __restrict__ groups, int64_t ngroups,
+                                                              RbkSum* __restrict__ gprefix,
+                                                              unsigned long long* __restrict__ gheads,
+                                                              Status* st) {
+    rbk_scan_body<kComp>(groups, ngroups, gprefix, gheads, st);
+}
+
 struct RbkEmitSmem {
     uint64_t row_key[kRbkTile + 1];        // closed segments of this tile, by row
     double row_val[kRbkTile + 1];
@@ -893,14 +1051,11 @@ template <class H>
 constexpr int rbk_emit_ctas() { return H::kBits ? 5 : 4; }
 
 template <bool kComp, class H, class Src>
-__global__ void __launch_bounds__(kRbkThreads, rbk_emit_ctas<H>()) k_rbk_emit(H hd, Src src, int64_t n,
-                                                             const RbkSum* __restrict__ ingroup,
-                                                             const RbkSum* __restrict__ gprefix,
-                                                             const unsigned long long* __restrict__ gheads,
-                                                             StreamDesc p, SegOut o, Status* st) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    RbkEmitSmem& sm = *reinterpret_cast<RbkEmitSmem*>(smem_raw);
-    const int64_t tile = blockIdx.x;
+__device__ __forceinline__ void rbk_emit_body(RbkEmitSmem& sm, const H& hd, const Src& src, int64_t n, int64_t tile,
+                                              const RbkSum* __restrict__ ingroup,
+                                              const RbkSum* __restrict__ gprefix,
+                                              const unsigned long long* __restrict__ gheads, const StreamDesc& p,
+                                              const SegOut& o, Status* st) {
     const int64_t ntiles = (n + kRbkTile - 1) / kRbkTile;
     RbkPairs r;
     rbk_load<kComp>(hd, src, n, tile, r);
@@ -993,6 +1148,18 @@ __global__ void __launch_bounds__(kRbkThreads, rbk_emit_ctas<H>()) k_rbk_emit(H 
         }
     }
 }
+
+template <bool kComp, class H, class Src>
+__global__ void __launch_bounds__(kRbkThreads, rbk_emit_ctas<H>()) k_rbk_emit(H hd, Src src, int64_t n,
+                                                             const RbkSum* __restrict__ ingroup,
+                                                             const RbkSum* __restrict__ gprefix,
+                                                             const unsigned long long* __restrict__ gheads,
+                                                             StreamDesc p, SegOut o, Status* st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RbkEmitSmem& sm = *reinterpret_cast<RbkEmitSmem*>(smem_raw);
+    rbk_emit_body<kComp>(sm, hd, src, n, (int64_t)blockIdx.x, ingroup, gprefix, gheads, p, o, st);
+}
+
 size_t rbk_state_bytes(int64_t n) {
     const int64_t ntiles = (std::max<int64_t>(n, 1) + kRbkTile - 1) / kRbkTile;
     const int64_t ngroups = (ntiles + kRbkGroup - 1) / kRbkGroup;
@@ -1055,5 +1222,112 @@ void launch_reduce_by_key_prepared(const uint8_t* head_bits, const uint64_t* row
     else rbk_launch<false>(BitHeads{head_bits, row_keys}, PrepTermsDev{terms}, n, state, p, o, st, stream);
 }
 
+
+// ---- the reduce-by-key stages over a batch ---------------------------------
+struct RbkState {
+    RbkSum* tiles;
+    RbkSum* ingroup;
+    RbkSum* groups;
+    RbkSum* gprefix;
+    unsigned long long* gheads;
+    int64_t ntiles, ngroups;
+};
+
+// The layout rbk_launch uses for state of n pairs.
+__host__ __device__ __forceinline__ RbkState rbk_state_of(void* state, int64_t n) {
+    RbkState r;
+    r.ntiles = (n + kRbkTile - 1) / kRbkTile;
+    r.ngroups = (r.ntiles + kRbkGroup - 1) / kRbkGroup;
+    r.tiles = static_cast<RbkSum*>(state);
+    r.ingroup = r.tiles + r.ntiles;
+    r.groups = r.ingroup + r.ntiles;
+    r.gprefix = r.groups + r.ngroups;
+    r.gheads = reinterpret_cast<unsigned long long*>(r.gprefix + r.ngroups);
+    return r;
+}
+
+int64_t rbk_tiles(int64_t n) { return (std::max<int64_t>(n, 1) + kRbkTile - 1) / kRbkTile; }
+int64_t rbk_groups(int64_t n) { return (rbk_tiles(n) + kRbkGroup - 1) / kRbkGroup; }
+
+// The sorted pairs of a job: the buffer its last digit pass wrote.
+__device__ __forceinline__ const uint64_t* job_keys(const BatchJob& J) { return J.keys[J.npass & 1]; }
+__device__ __forceinline__ const double* job_vals(const BatchJob& J) { return J.vals[J.npass & 1]; }
+
+template <bool kComp>
+__global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles_batch(const BatchJob* __restrict__ jobs, JobList l) {
+    __shared__ int s_pos;
+    if (threadIdx.x == 0) s_pos = job_of(l.prefix, l.count, blockIdx.x);
+    __syncthreads();
+    const int pos = s_pos;
+    const BatchJob& J = jobs[__ldg(l.idx + pos)];
+    const int64_t tile = blockIdx.x - __ldg(l.prefix + pos);
+    const RbkState rs = rbk_state_of(J.rbk_state, J.p.nnz);
+    rbk_tiles_body<kComp>(KeyHeads{job_keys(J)}, PairTerms{job_vals(J)}, J.p.nnz, tile, rs.tiles + tile);
+}
+
+// One warp per group; l counts groups.
+template <bool kComp>
+__global__ void __launch_bounds__(256) k_rbk_groups_batch(const BatchJob* __restrict__ jobs, JobList l) {
+    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= __ldg(l.prefix + l.count)) return;
+    const int pos = job_of(l.prefix, l.count, w);
+    const BatchJob& J = jobs[__ldg(l.idx + pos)];
+    const RbkState rs = rbk_state_of(J.rbk_state, J.p.nnz);
+    rbk_group_body<kComp>(rs.tiles, rs.ntiles, rs.ingroup, rs.groups, (int64_t)(w - __ldg(l.prefix + pos)),
+                          threadIdx.x & 31);
+}
+
+// One CTA per problem.
+template <bool kComp>
+__global__ void __launch_bounds__(kRbkScanThreads) k_rbk_scan_batch(const BatchJob* __restrict__ jobs, JobList l) {
+    const BatchJob& J = jobs[__ldg(l.idx + blockIdx.x)];
+    const RbkState rs = rbk_state_of(J.rbk_state, J.p.nnz);
+    rbk_scan_body<kComp>(rs.groups, rs.ngroups, rs.gprefix, rs.gheads, J.p.status);
+}
+
+template <bool kComp>
+__global__ void __launch_bounds__(kRbkThreads, rbk_emit_ctas<KeyHeads>()) k_rbk_emit_batch(
+    const BatchJob* __restrict__ jobs, JobList l) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RbkEmitSmem& sm = *reinterpret_cast<RbkEmitSmem*>(smem_raw);
+    __shared__ int s_pos;
+    if (threadIdx.x == 0) s_pos = job_of(l.prefix, l.count, blockIdx.x);
+    __syncthreads();
+    const int pos = s_pos;
+    const BatchJob& J = jobs[__ldg(l.idx + pos)];
+    const int64_t tile = blockIdx.x - __ldg(l.prefix + pos);
+    const RbkState rs = rbk_state_of(J.rbk_state, J.p.nnz);
+    rbk_emit_body<kComp>(sm, KeyHeads{job_keys(J)}, PairTerms{job_vals(J)}, J.p.nnz, tile, rs.ingroup, rs.gprefix,
+                         rs.gheads, J.p, J.o, J.p.status);
+}
+
+template <bool kComp>
+static void rbk_batch(const BatchJob* jobs, const JobList& tiles, uint32_t ntiles, const JobList& groups,
+                      uint32_t ngroup_warps, cudaStream_t stream) {
+    const size_t smem = sizeof(RbkEmitSmem);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_rbk_emit_batch<kComp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_rbk_emit_batch<kComp>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        attr_set = true;
+    }
+    TTV_LAUNCH("rbk_tiles_batch", stream, k_rbk_tiles_batch<kComp><<<ntiles, kRbkThreads, 0, stream>>>(jobs, tiles));
+    TTV_LAUNCH("rbk_groups_batch", stream,
+               k_rbk_groups_batch<kComp><<<(ngroup_warps * 32 + 255) / 256, 256, 0, stream>>>(jobs, groups));
+    TTV_LAUNCH("rbk_scan_batch", stream,
+               k_rbk_scan_batch<kComp><<<(unsigned)tiles.count, kRbkScanThreads, 0, stream>>>(jobs, tiles));
+    TTV_LAUNCH("rbk_emit_batch", stream,
+               k_rbk_emit_batch<kComp><<<ntiles, kRbkThreads, smem, stream>>>(jobs, tiles));
+}
+
+// tiles counts reduce-by-key tiles, groups their groups of 32 (one warp
+// each), both over the same problems in the same order.
+void launch_rbk_batch(const BatchJob* jobs, const JobList& tiles, uint32_t ntiles, const JobList& groups,
+                      uint32_t ngroup_warps, bool compensated, cudaStream_t stream) {
+    if (tiles.count <= 0 || ntiles == 0) return;
+    if (compensated) rbk_batch<true>(jobs, tiles, ntiles, groups, ngroup_warps, stream);
+    else rbk_batch<false>(jobs, tiles, ntiles, groups, ngroup_warps, stream);
+}
 
 }  // namespace ttv

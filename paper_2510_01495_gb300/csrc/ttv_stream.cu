@@ -54,7 +54,7 @@ void launch_keys_terms(const StreamDesc& p, uint64_t* keys, double* terms, cudaS
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = p.vec_smem ? (size_t)p.vtotal * sizeof(double) : 0;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_keys_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_at_least(k_keys_terms, smem);
     const int64_t want = (p.nnz + kStreamThreads * kUnroll - 1) / (kStreamThreads * kUnroll);
     const int per_sm = p.ctas_per_sm > 0 ? p.ctas_per_sm : 8;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * per_sm));
@@ -245,10 +245,10 @@ int dense_grid(const StreamDesc& p, int want_presence) {
     const size_t smem = dense_layout(p, want_presence).total;
     int per_sm = 1;
     if (use_int_products(p)) {
-        cudaFuncSetAttribute(k_dense_accum<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+        smem_at_least(k_dense_accum<true>, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_accum<true>, kStreamThreads, smem);
     } else {
-        cudaFuncSetAttribute(k_dense_accum<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+        smem_at_least(k_dense_accum<false>, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_accum<false>, kStreamThreads, smem);
     }
     per_sm = std::max(1, std::min(per_sm, p.ctas_per_sm > 0 ? p.ctas_per_sm : 4));
@@ -266,11 +266,11 @@ void launch_dense(const StreamDesc& p, int want_presence, int compensated, int G
     if (dense_vec_applicable(p)) {
         launch_dense_vec(p, want_presence, G, partials, pres_partials, stream);
     } else if (use_int_products(p)) {
-        cudaFuncSetAttribute(k_dense_accum<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(L.total, 1));
+        smem_at_least(k_dense_accum<true>, L.total);
         TTV_LAUNCH("dense_accum", stream, k_dense_accum<true><<<G, kStreamThreads, L.total, stream>>>(
                                               p, chunk, want_presence, L.pres_off, L.vec_off, partials, pres_partials));
     } else {
-        cudaFuncSetAttribute(k_dense_accum<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(L.total, 1));
+        smem_at_least(k_dense_accum<false>, L.total);
         TTV_LAUNCH("dense_accum", stream, k_dense_accum<false><<<G, kStreamThreads, L.total, stream>>>(
                                               p, chunk, want_presence, L.pres_off, L.vec_off, partials, pres_partials));
     }

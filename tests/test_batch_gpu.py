@@ -59,3 +59,77 @@ def test_batch_mixed_orders_and_dense(cuda_lib):
         for (subs, vals, shape, modes, vecs), r in zip(items, res):
             ref, A = oracle_ttv(subs, vals, shape, modes, vecs, dense=(fmt == "dense"))
             check_result(r, ref, A, dense=(fmt == "dense"))
+
+
+def _items(ps, dev="cuda", soa_every=0):
+    """Device copies; every soa_every-th problem gets d contiguous columns
+    (an odd nnz gives an odd column stride: the key kernel's any-stride form)."""
+    items = []
+    for j, p in enumerate(ps):
+        t = p.tensor
+        subs = t.subs.to(dev)
+        if soa_every and j % soa_every == 0:
+            subs = subs.t().contiguous().t()
+        items.append((subs, t.vals.to(dev), t.shape, p.modes, [v.to(dev) for v in p.vecs]))
+    return items
+
+
+@pytest.mark.parametrize("accum", ["fp64", "compensated"])
+def test_batch_stagewise_sort_path(cuda_lib, accum):
+    """Sort-path problems run stage by stage: the whole batch is a fixed
+    handful of kernel launches (key kernels per order and layout class: 3
+    orders x 3 classes here; one histogram scan, at most 8 digit passes, 4
+    reduce-by-key stages), every result matches the oracle, and a replay is
+    bit-identical."""
+    ps = _problems(40, 11, scale=0.003)
+    items = _items(ps, soa_every=3)
+    soa = [it[0].stride(1) for it in items if it[0].stride(0) == 1]
+    assert any(s % 2 for s in soa) and any(s % 2 == 0 for s in soa)
+    b = cuda_lib.Batch(items, fmt="sparse", path="sort", accum=accum)
+    r1 = b.run()
+    assert 0 < b.graph_launches() <= 9 + 1 + 8 + 4, b.graph_launches()
+    for p, it, r in zip(ps, items, r1):
+        ref, A = oracle_ttv(*it, dense=False)
+        check_result(r, ref, A, dense=False, what=p.name)
+    first = [(r.subs.clone(), r.vals.clone()) for r in r1]
+    r2 = b.run()
+    for (s1, v1), r in zip(first, r2):
+        assert torch.equal(s1, r.subs) and torch.equal(v1, r.vals)
+
+
+def test_batch_stagewise_mixed_with_other_paths(cuda_lib):
+    """Sort-path problems of uneven size beside small dense-path ones in one
+    graph: each result matches the oracle."""
+    ps = _problems(16, 13, scale=0.01)
+    items = _items(ps, soa_every=2)
+    g = np.random.default_rng(9)
+    for i in range(6):
+        shape = tuple(int(x) for x in g.integers(4, 20, size=3))
+        t = S.sptenrand(700 + i, shape, int(np.prod(shape)) // 3, vals="u11")
+        items.append((t.subs.cuda(), t.vals.cuda(), shape, [i % 3], [S.vector(700 + i, i % 3, shape[i % 3]).cuda()]))
+    b = cuda_lib.Batch(items, fmt="sparse")
+    res = b.run()
+    for it, r in zip(items, res):
+        ref, A = oracle_ttv(*it, dense=False)
+        check_result(r, ref, A, dense=False)
+
+
+def test_batch_stagewise_subscript_error(cuda_lib):
+    """A subscript outside its mode in one problem of a stage-wise batch
+    makes the batch report TTV_ERR_SUBSCRIPT; the context stays usable."""
+    from paper_2510_01495_gb300 import TTVError
+    ps = _problems(8, 17, scale=0.002)
+    items = _items(ps)
+    subs, vals, shape, modes, vecs = items[3]
+    bad = subs.clone()
+    bad[bad.shape[0] // 2, 0] = shape[0]
+    items[3] = (bad, vals, shape, modes, vecs)
+    b = cuda_lib.Batch(items, fmt="sparse", path="sort")
+    with pytest.raises(TTVError) as ei:
+        b.run()
+    assert ei.value.name == "TTV_ERR_SUBSCRIPT"
+    good = _items(ps[:3])
+    res = cuda_lib.Batch(good, fmt="sparse", path="sort").run()
+    for it, r in zip(good, res):
+        ref, A = oracle_ttv(*it, dense=False)
+        check_result(r, ref, A, dense=False)
