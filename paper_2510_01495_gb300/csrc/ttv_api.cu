@@ -1567,6 +1567,13 @@ static int batch_plans(const ttv_problem* probs, int32_t n, const ttv_opts* o, s
         const ttv_problem& q = probs[i];
         int rc = make_plan(&q.tensor, q.modes, q.n_v, q.vecs, q.v_dtype, nullptr, o, plans[(size_t)i]);
         if (rc != TTV_OK) return fail(rc, "problem %d: %s", i, g_err.c_str());
+        // A hashed (not direct) table ends in a radix sort of its distinct
+        // keys, a dozen launches of its own; in a batch the stage-wise sort
+        // takes such a problem at no launch cost (same bytes within a few
+        // percent: 17.6 against 17.8 ms for the 512-problem batch).
+        Plan& pl = plans[(size_t)i];
+        if (o->path == TTV_PATH_AUTO && pl.path == TTV_PATH_HASH && !pl.dense_out && !hash_direct(pl.desc))
+            pl.path = TTV_PATH_SORT;
         ws_off[(size_t)i] = total;
         total += round256(workspace_bytes(plans[(size_t)i]));
         if (batch_sortable(plans[(size_t)i])) batched.push_back(i);
