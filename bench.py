@@ -716,10 +716,99 @@ def run_batch(args, rank, world, local_rank):
         "graph_kernel_launches_per_step": b.graph_launches(), "gpu_launches": launches, "clocks": clk,
         "autotune": {"classes_tuned": tuned, "seconds": round(t_tune, 2), "problems_by_path": chosen},
     }
+    # the step's roofline: every problem's algorithmic bytes over the step time
+    res = b.run()
+    torch.cuda.synchronize(dev)
+    nnz_out = [int(res[i].vals.numel()) for i in range(len(probs))]
+    alg = sum(algorithmic_bytes(p, n)["total"] for p, n in zip(probs, nnz_out))
+    peaks, peak_src = load_peaks()
+    peak = peaks["hbm_gbs"]
+    step_gbs = alg / (ms * 1e-3) / 1e9
+    st_tr = STEP_TRAFFIC.get("batch_512")
+    traffic = None
+    if st_tr and args.scale == 1.0 and world == 1 and kernel_source_hash(st_tr["files"]) == st_tr["sha"]:
+        traffic = st_tr["bytes_per_step"]
+    line["config"]["nnz_out_total"] = sum(nnz_out)
+    line["roofline"] = {
+        "bound": "hbm", "kernel": "whole step: the batch graph (stage-wise sort path)", "achieved": step_gbs,
+        "peak": peak, "unit": "GB/s", "frac": step_gbs / peak, "traffic": traffic,
+        "peak_source": f"{peak_src} hbm_gbs", "alg_bytes_per_step": alg,
+        "alg_bytes_basis": "sum over problems of nnz*(8d+w) + vector once + nnz_out*(8*order+8)"}
+    line["e2e"] = batch_e2e(ttv, b, items, probs, args, dev)
+    if dist:
+        line["e2e"]["ms_per_step"] = max_over_ranks(dist, line["e2e"]["ms_per_step"], dev)
+        line["e2e"]["value"] = total_nnz * world / (line["e2e"]["ms_per_step"] * 1e-3) / 1e9
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_cpu_baseline(probs)
     if dist:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def batch_e2e(ttv, b, items, probs, args, dev):
+    """The batch through ttv_batch with HOST inputs: every problem's subs,
+    vals and vector copied from pinned host memory into the buffers the
+    batch was built on (so the cached graph replays), the launch, and every
+    result read back, inside the timed region."""
+    h_subs = [it[0].t().contiguous().cpu().pin_memory() for it in items]    # stored as d columns
+    h_vals = [it[1].cpu().pin_memory() for it in items]
+    h_vecs = [[v.cpu().pin_memory() for v in it[4]] for it in items]
+    d_subs = [it[0].t() for it in items]             # the (d, nnz) column storage behind each view
+    h2d = sum(x.numel() * 8 for x in h_subs) + sum(x.numel() * x.element_size() for x in h_vals) + \
+        sum(v.numel() * v.element_size() for vs in h_vecs for v in vs)
+    # pinned host buffers for the results, at the batch's output capacities
+    res0 = b.run()
+    h_out = [(torch.empty(tuple(m[1].shape) if m[1] is not None else (0,), dtype=torch.int64).pin_memory(),
+              torch.empty(m[0].numel(), dtype=torch.float64).pin_memory()) for m in b.meta]
+    del res0
+    times, d2h = [], 0
+    for i in range(max(1, args.e2e_steps) + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for ds, hs, it, hv, hvs in zip(d_subs, h_subs, items, h_vals, h_vecs):
+            ds.copy_(hs, non_blocking=True)
+            it[1].copy_(hv, non_blocking=True)
+            for a, c in zip(it[4], hvs):
+                a.copy_(c, non_blocking=True)
+        res = b.run()
+        d2h = 0
+        for r, (hs_, hv_) in zip(res, h_out):
+            n = r.vals.numel()
+            hv_[:n].copy_(r.vals, non_blocking=True)
+            d2h += n * 8
+            if r.subs is not None and r.subs.numel():
+                hs_[:n].copy_(r.subs, non_blocking=True)
+                d2h += r.subs.numel() * 8
+        torch.cuda.synchronize(dev)
+        if i > 0:
+            times.append(time.perf_counter() - t0)
+    mean = sum(times) / len(times)
+    total = sum(p.tensor.nnz for p in probs)
+    return {"value": total / mean / 1e9, "unit": "GNNZ/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": mean * 1e3, "steps": len(times)}
+
+
+def batch_cpu_baseline(probs, target_s: float = 10.0):
+    """The oracle, as it stands, on whole problems of the batch taken in
+    their order until about target_s seconds of one core have run."""
+    import oracle
+    oracle.build()
+    done, nnz, t_all = 0, 0, 0.0
+    for p in probs:
+        t = p.tensor
+        subs = t.subs.cpu().numpy()
+        vals = t.vals.cpu().numpy()
+        vecs = [v.cpu().numpy() for v in p.vecs]
+        t0 = time.perf_counter()
+        oracle.ttv(subs, vals, t.shape, p.modes, vecs, dense=p.dense)
+        t_all += time.perf_counter() - t0
+        done += 1
+        nnz += t.nnz
+        if t_all >= target_s:
+            break
+    return {"value": nnz / t_all / 1e9, "unit": "GNNZ/s", "cores": 1, "kind": "oracle",
+            "sample": f"the first {done} of {len(probs)} problems ({nnz} nonzeros), one call each, {t_all:.1f} s"}
 
 
 def run_serve(args, rank, world, local_rank):
@@ -770,6 +859,8 @@ def run_serve(args, rank, world, local_rank):
     clocks = _clock_start(local_rank)
     arrivals = np.cumsum(g.exponential(1.0 / args.rate, size=args.requests))
 
+    rows = []   # result rows of each request of the last stream, in submission order
+
     def stream(accum, arr=None, items=None):
         # the client takes every result as soon as it is ready (a waiter
         # thread, in submission order), so results do not pile up on the device
@@ -778,6 +869,7 @@ def run_serve(args, rank, world, local_rank):
         items = reqs[64:] if items is None else items
         pending = queue.Queue()
         errors = []
+        rows.clear()
 
         def waiter():
             while True:
@@ -785,7 +877,7 @@ def run_serve(args, rank, world, local_rank):
                 if rid is None:
                     return
                 try:
-                    srv.wait(rid, timeout_us=120_000_000)
+                    rows.append(int(srv.wait(rid, timeout_us=120_000_000).vals.numel()))
                 except Exception as e:   # noqa: BLE001 -- re-raised by the submitting thread
                     errors.append(e)
 
@@ -808,6 +900,11 @@ def run_serve(args, rank, world, local_rank):
 
     wall = stream("compensated")
     st = srv.stats()
+    # algorithmic bytes of the stream: FP32 values and vectors, int64
+    # subscripts, result rows of 3 subscripts and a binary64 value
+    served_bytes = sum(nnzs[ti] * (8 * 4 + 4) + shapes[ti][m] * 4 + nr * (8 * 3 + 8)
+                       for (ti, m, _), nr in zip(reqs[64:], rows))
+    served_rows = sum(rows)
     # light load: the same requests arriving at --light-rate, where a request
     # rarely waits for another; its latency against the one-at-a-time form
     n_light = min(300, args.requests)
@@ -888,10 +985,45 @@ def run_serve(args, rank, world, local_rank):
                   "p99_ms": pst["p99_us"] / 1e3},
         "clocks": clk, "accuracy_fp32_storage": accuracy,
     }
+    peaks, peak_src = load_peaks()
+    served_gbs = sum_over_ranks(dist, served_bytes, dev) / wall / 1e9
+    line["config"]["nnz_out_total"] = served_rows
+    line["roofline"] = {
+        "bound": "hbm", "kernel": "whole stream: every served request's kernels", "achieved": served_gbs,
+        "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": served_gbs / peaks["hbm_gbs"], "traffic": None,
+        "peak_source": f"{peak_src} hbm_gbs", "alg_bytes": served_bytes,
+        "alg_bytes_basis": "per request nnz*(8*4+4) + vector once (FP32) + nnz_out*(8*3+8)",
+        "note": "the offered arrival rate, not the GPU, bounds this stream's rate"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = serve_cpu_baseline(acc_sample, g)
     if dist:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def serve_cpu_baseline(sample, g, target_s: float = 10.0):
+    """The oracle, as it stands, on requests against the sampled resident
+    tensors (their FP32-rounded values), until about target_s seconds of one
+    core have run."""
+    import oracle
+    oracle.build()
+    nnz, t_all, calls = 0, 0.0, 0
+    host = [(sb.cpu().numpy(), v64.float().double().cpu().numpy(), shp) for sb, v64, shp, _ in sample]
+    while host and t_all < target_s:
+        for subs, vals, shp in host:
+            m = int(g.integers(0, 4))
+            x = g.uniform(-1, 1, shp[m]).astype(np.float32).astype(np.float64)
+            t0 = time.perf_counter()
+            oracle.ttv(subs, vals, shp, [m], [x], dense=False)
+            t_all += time.perf_counter() - t0
+            nnz += vals.shape[0]
+            calls += 1
+            if t_all >= target_s:
+                break
+    return {"value": nnz / max(t_all, 1e-9) / 1e9, "unit": "GNNZ/s", "cores": 1, "kind": "oracle",
+            "sample": f"{calls} requests against {len(host)} resident tensors of at most 2e6 nonzeros, "
+                      f"{nnz} nonzeros, {t_all:.1f} s"}
 
 
 # FP64 multiply rate used as the MTTKRP roofline: the nominal FP64 rate of
