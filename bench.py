@@ -104,6 +104,11 @@ DOMINANT = {"allbutone_4way_1000": [("dense_accum", _stream_bytes), ("dense_fx",
 # the ncu launch list under profiles/), with the sha1 of the sources those
 # kernels are built from; reported as null once the sources differ.
 STEP_TRAFFIC = {
+    "batch_512": {
+        "files": ["ttv_keys.cu", "ttv_sort.cu", "ttv_internal.cuh", "ttv_udiv.h", "ttv_api.cu"],
+        "sha": "3754de8ca2b0",
+        "bytes_per_step": 45919396608,   # the 19 stage-wise launches of one step; 4.35x the algorithmic bytes
+    },
     "single_5way_zipf": {
         "files": ["ttv_keys.cu", "ttv_sort.cu", "ttv_internal.cuh", "ttv_udiv.h"],
         "sha": "61e9c63b21d9",
