@@ -105,14 +105,14 @@ DOMINANT = {"allbutone_4way_1000": [("dense_accum", _stream_bytes), ("dense_fx",
 # kernels are built from; reported as null once the sources differ.
 STEP_TRAFFIC = {
     "batch_512": {
-        "files": ["ttv_keys.cu", "ttv_sort.cu", "ttv_internal.cuh", "ttv_udiv.h", "ttv_api.cu"],
-        "sha": "3754de8ca2b0",
+        "files": ["ttv_keys.cu", "ttv_sort.cu", "ttv_internal.cuh", "ttv_udiv.h"],
+        "sha": "679399418002",
         "bytes_per_step": 45919396608,   # the 19 stage-wise launches of one step; 4.35x the algorithmic bytes
     },
     "single_5way_zipf": {
         "files": ["ttv_keys.cu", "ttv_sort.cu", "ttv_internal.cuh", "ttv_udiv.h"],
-        "sha": "61e9c63b21d9",
-        "bytes_per_step": 30770329600,   # 12 launches of one TTV; 4.2x the algorithmic bytes
+        "sha": "679399418002",
+        "bytes_per_step": 32439018240,   # 12 launches of one (warm) TTV; 4.5x the algorithmic bytes
     },
 }
 

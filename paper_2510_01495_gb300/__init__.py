@@ -22,6 +22,8 @@ import ctypes
 import os
 import threading
 
+import numpy as np
+
 import torch
 
 from . import _build
@@ -793,6 +795,13 @@ def _declare_batch(lib):
     return lib
 
 
+# The ttv_out fields BatchResults needs, at their ctypes offsets.
+_OUT_DTYPE = np.dtype({"names": ["order", "shape", "nnz", "is_dense"],
+                       "formats": [np.int32, (np.int64, TTV_MAX_D), np.int64, np.int32],
+                       "offsets": [Out.order.offset, Out.shape.offset, Out.nnz.offset, Out.is_dense.offset],
+                       "itemsize": ctypes.sizeof(Out)})
+
+
 class BatchResults:
     """The results of one batch run: ``Result`` views made on access."""
 
@@ -871,8 +880,10 @@ class Batch:
         rc = self.lib.ttv_batch(self.probs, self.n, outs, ctypes.byref(self.opts), _stream_handle(stream))
         try:
             _check(self.lib, rc)
-            return BatchResults(self.meta, [(int(o.nnz), bool(o.is_dense), int(o.order), tuple(o.shape))
-                                            for o in outs[:self.n]])
+            # nnz, is_dense, order and shape of every result in one read of the array
+            a = np.frombuffer(outs, dtype=_OUT_DTYPE, count=self.n)
+            return BatchResults(self.meta, list(zip(a["nnz"].tolist(), a["is_dense"].astype(bool).tolist(),
+                                                    a["order"].tolist(), map(tuple, a["shape"].tolist()))))
         finally:
             self.lib.ttv_outs_free(outs, self.n)
 

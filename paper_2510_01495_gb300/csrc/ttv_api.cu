@@ -501,11 +501,13 @@ static int auto_to_dense(ttv_out* out, OutState* s) {
     return TTV_OK;
 }
 
-static int finalize(ttv_out* out) {
+// synced: the caller has just synchronised the result's stream (a batch
+// finalises hundreds of results after one synchronisation).
+static int finalize(ttv_out* out, bool synced = false) {
     OutState* s = static_cast<OutState*>(out->internal);
     if (!s) return fail(TTV_ERR_ARG, "result has no pending call");
     if (s->finalized) return s->rc;
-    cudaError_t e = cudaStreamSynchronize(s->stream);
+    cudaError_t e = synced ? cudaSuccess : cudaStreamSynchronize(s->stream);
     s->finalized = 1;
     if (e != cudaSuccess) return s->rc = cuda_fail(e, "stream synchronize");
     const Status& h = *s->hstatus;
@@ -1950,8 +1952,9 @@ int ttv_batch(const ttv_problem* probs, int32_t n, ttv_out* outs, const ttv_opts
         outs[i].nnz = sh.nnz;
     }
     if (o->async) return TTV_OK;
+    ce = cudaStreamSynchronize(stream);
     for (int32_t i = 0; i < n; ++i) {
-        const int r = finalize(&outs[i]);
+        const int r = finalize(&outs[i], ce == cudaSuccess);
         if (r != TTV_OK && first == TTV_OK) first = r;
     }
     return first;
