@@ -133,3 +133,47 @@ def test_batch_stagewise_subscript_error(cuda_lib):
     for it, r in zip(good, res):
         ref, A = oracle_ttv(*it, dense=False)
         check_result(r, ref, A, dense=False)
+
+
+def test_batch_stagewise_f32_tiny_and_order2(cuda_lib):
+    """FP32 values and vectors on the stage-wise path (both sides see the
+    same float values, upcast exactly: the FP64 tolerance), beside problems
+    of 0, 1, 2 and 3 nonzeros and order-2 tensors."""
+    g = np.random.default_rng(23)
+    items = []
+    for i, p in enumerate(_problems(10, 19, scale=0.004)):
+        t = p.tensor
+        subs = t.subs.cuda()
+        if i % 2:
+            subs = subs.t().contiguous().t()
+        items.append((subs, t.vals.float().cuda(), t.shape, p.modes, [v.float().cuda() for v in p.vecs]))
+    for i, nnz in enumerate([0, 1, 2, 3, 5000, 777]):
+        d = 2 if i >= 4 else 3
+        shape = tuple(int(x) for x in g.integers(200, 3000, size=d))
+        t = S.sptenrand(900 + i, shape, nnz, vals="u11")
+        m = int(g.integers(0, d))
+        items.append((t.subs.cuda(), t.vals.cuda(), shape, [m], [S.vector(900 + i, m, shape[m]).cuda()]))
+    b = cuda_lib.Batch(items, fmt="sparse", path="sort")
+    res = b.run()
+    for it, r in zip(items, res):
+        subs, vals, shape, modes, vecs = it
+        ref, A = oracle_ttv(subs, vals.double(), shape, modes, [v.double() for v in vecs], dense=False)
+        check_result(r, ref, A, dense=False)
+
+
+def test_batch_stagewise_capacity_error(cuda_lib):
+    """A result buffer with fewer rows than a stage-wise problem's result
+    makes the batch report TTV_ERR_CAPACITY (rows past the buffer are not
+    written)."""
+    from paper_2510_01495_gb300 import TTVError
+    ps = _problems(6, 29, scale=0.003)
+    items = _items(ps)
+    b = cuda_lib.Batch(items, fmt="sparse", path="sort")
+    ov, os_, shape, modes = b.meta[2]
+    half = max(1, ov.numel() // 2)
+    guard = torch.full((half + 64,), 7.0, dtype=torch.float64, device=ov.device)
+    b.meta[2] = (guard[:half], os_[:half], shape, modes)
+    with pytest.raises(TTVError) as ei:
+        b.run()
+    assert ei.value.name == "TTV_ERR_CAPACITY"
+    assert torch.all(guard[half:] == 7.0)
