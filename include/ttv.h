@@ -375,10 +375,18 @@ int ttv_matvec_workspace_size(int64_t n1, int64_t n2, int64_t stride_row, int64_
  * queue up; a scheduler thread admits any queued request for which a stream
  * slot is free and the memory budget covers its workspace, result and
  * vectors (a request that does not fit yet does not block smaller ones behind
- * it), so the work of several requests overlaps on the GPU.  Latency is
- * measured from submit to completion on the GPU.  Results are
+ * it), so the work of several requests overlaps on the GPU.  While more
+ * requests wait than slots are free, a free slot takes a group of queued
+ * requests with the same options (up to 32, about the queue over the free
+ * slots) and runs them as one stage-wise batch (see ttv_batch): the sort-path
+ * requests of a group share one launch per stage.  Requests on a prepared
+ * layout always run alone.  Latency is measured from submit to completion on
+ * the GPU (a group's requests complete together).  Results are
  * library-allocated device buffers handed over by ttv_server_wait (release
- * with ttv_out_free); they stop counting against the budget once complete. */
+ * with ttv_out_free); from completion until claimed only the result counts
+ * against the budget.  While unclaimed results keep the budget full, the
+ * oldest queued request is still admitted whenever nothing runs, so a client
+ * waiting by id always progresses. */
 typedef struct ttv_server ttv_server;
 
 typedef struct {
@@ -388,9 +396,11 @@ typedef struct {
     double throughput_rps, throughput_gnnz_s; /* completed requests / nonzeros    */
     size_t bytes_in_use, budget_bytes;
     long long prepared_runs;                  /* requests served from a prepared layout */
+    long long grouped_runs;                   /* requests served inside a group of two or more */
 } ttv_stats;
 
-/* budget_bytes bounds resident tensors + in-flight requests; n_slots (1..64)
+/* budget_bytes bounds resident tensors + in-flight requests + unclaimed
+ * results (bytes_in_use in ttv_stats); n_slots (1..64)
  * concurrent requests, one CUDA stream each. */
 int ttv_server_create(size_t budget_bytes, int32_t n_slots, ttv_server **server);
 /* Copies a device tensor (any subscript strides) into the server; it counts
@@ -417,6 +427,14 @@ int ttv_server_submit(ttv_server *server, int32_t tensor_id, const int32_t *mode
 /* Waits up to timeout_us (< 0: forever) for a request and moves its result
  * into *out.  TTV_ERR_TIMEOUT if it is not done in time. */
 int ttv_server_wait(ttv_server *server, uint64_t req_id, int64_t timeout_us, ttv_out *out);
+/* Waits up to timeout_us (< 0: forever) for any finished request not yet
+ * claimed (the oldest first) and moves its id into *req_id and its result
+ * into *out; for a client that takes results as they finish, whatever order
+ * they finish in (an unclaimed result holds budget, so claiming in
+ * submission order behind a slow request holds back admission).  A server's
+ * clients should use one of the two waits, not both: this one may take a
+ * request another thread waits on by id. */
+int ttv_server_wait_any(ttv_server *server, int64_t timeout_us, uint64_t *req_id, ttv_out *out);
 int ttv_server_stats(ttv_server *server, ttv_stats *stats);
 /* Clears latencies and counters (e.g. after a warm-up). */
 int ttv_server_reset_stats(ttv_server *server);

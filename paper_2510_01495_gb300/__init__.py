@@ -18,9 +18,12 @@ input); dense results are row-major arrays of shape[R].
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import sys
 import threading
+import weakref
 
 import numpy as np
 
@@ -905,7 +908,7 @@ class Stats(ctypes.Structure):
                 ("refused", ctypes.c_longlong), ("pending", ctypes.c_longlong), ("seconds", ctypes.c_double),
                 ("throughput_rps", ctypes.c_double), ("throughput_gnnz_s", ctypes.c_double),
                 ("bytes_in_use", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
-                ("prepared_runs", ctypes.c_longlong)]
+                ("prepared_runs", ctypes.c_longlong), ("grouped_runs", ctypes.c_longlong)]
 
 
 def _declare_serve(lib):
@@ -923,6 +926,8 @@ def _declare_serve(lib):
     lib.ttv_server_submit.restype = ctypes.c_int
     lib.ttv_server_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, P(Out)]
     lib.ttv_server_wait.restype = ctypes.c_int
+    lib.ttv_server_wait_any.argtypes = [ctypes.c_void_p, ctypes.c_int64, P(ctypes.c_uint64), P(Out)]
+    lib.ttv_server_wait_any.restype = ctypes.c_int
     lib.ttv_server_stats.argtypes = [ctypes.c_void_p, P(Stats)]
     lib.ttv_server_stats.restype = ctypes.c_int
     lib.ttv_server_reset_stats.argtypes = [ctypes.c_void_p]
@@ -939,6 +944,50 @@ class _DeviceArray:
     def __init__(self, ptr, shape, typestr):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
                                          "version": 2, "strides": None}
+
+
+class _OwnedOut:
+    """A library-owned result, released (ttv_out_free) when the last tensor
+    viewing it is gone; torch's current stream is synchronised first, so work
+    queued on the views has finished."""
+
+    def __init__(self, lib, out: Out):
+        self.lib, self.out = lib, out
+
+    def __del__(self):
+        if sys.is_finalizing():   # the runtime may be gone; the process frees everything
+            return
+        try:
+            torch.cuda.current_stream().synchronize()
+            self.lib.ttv_out_free(ctypes.byref(self.out))
+        except Exception:   # noqa: BLE001
+            pass
+
+
+class _OwnedArray(_DeviceArray):
+    def __init__(self, owner, ptr, shape, typestr):
+        super().__init__(ptr, shape, typestr)
+        self.owner = owner       # torch.as_tensor keeps this object, hence the result, alive
+
+
+def _view_result(lib, out: Out) -> Result:
+    """A library-owned result as torch views of its buffers (no copy); the
+    buffers are released when the views are."""
+    owner = _OwnedOut(lib, out)
+    newshape = tuple(int(out.shape[j]) for j in range(out.order))
+    n = int(out.nnz)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if n > 0 and out.vals:
+        vals = torch.as_tensor(_OwnedArray(owner, out.vals, (n,), "<f8"), device=dev)
+    else:
+        vals = torch.zeros(n, dtype=torch.float64, device=dev)
+    if out.is_dense:
+        return Result(None, vals.view(newshape), newshape, True)
+    if out.order > 0 and n > 0 and out.subs:
+        subs = torch.as_tensor(_OwnedArray(owner, out.subs, (n, out.order), "<i8"), device=dev)
+    else:
+        subs = torch.zeros((n, out.order), dtype=torch.int64, device=dev)
+    return Result(subs, vals, newshape, False)
 
 
 def _take_result(lib, out: Out) -> Result:
@@ -965,6 +1014,20 @@ def _take_result(lib, out: Out) -> Result:
         lib.ttv_out_free(ctypes.byref(out))
 
 
+# Servers still open when the interpreter exits are closed first (their
+# scheduler threads must stop before the CUDA runtime is torn down).
+_live_servers = weakref.WeakSet()
+
+
+@atexit.register
+def _close_servers():
+    for srv in list(_live_servers):
+        try:
+            srv.close()
+        except Exception:   # noqa: BLE001
+            pass
+
+
 class Server:
     """Continuous-batching TTV server (``ttv_server_*``): resident tensors,
     requests admitted by memory budget onto ``slots`` concurrent streams."""
@@ -973,6 +1036,7 @@ class Server:
         self.lib = _declare_serve(load())
         self.h = ctypes.c_void_p()
         _check(self.lib, self.lib.ttv_server_create(int(budget_bytes), int(slots), ctypes.byref(self.h)))
+        _live_servers.add(self)
         self.shapes = {}
 
     def register(self, subs, vals, shape) -> int:
@@ -1002,7 +1066,9 @@ class Server:
                                                     1 if dt == np.float32 else 0, ctypes.byref(o), ctypes.byref(rid)))
         return int(rid.value)
 
-    def wait(self, req_id: int, timeout_us: int = -1) -> Result:
+    def wait(self, req_id: int, timeout_us: int = -1, copy: bool = True) -> Result:
+        """The result of request req_id: copied into torch memory (copy=True),
+        or views of the library's buffers, released with them (copy=False)."""
         out = Out()
         rc = self.lib.ttv_server_wait(self.h, int(req_id), int(timeout_us), ctypes.byref(out))
         if rc != 0:
@@ -1010,7 +1076,20 @@ class Server:
             if out.internal:
                 self.lib.ttv_out_free(ctypes.byref(out))
             raise TTVError(rc, msg)
-        return _take_result(self.lib, out)
+        return _take_result(self.lib, out) if copy else _view_result(self.lib, out)
+
+    def wait_any(self, timeout_us: int = -1, copy: bool = True):
+        """The next finished request, whichever it is: (request id, Result);
+        copy as for wait."""
+        out = Out()
+        rid = ctypes.c_uint64()
+        rc = self.lib.ttv_server_wait_any(self.h, int(timeout_us), ctypes.byref(rid), ctypes.byref(out))
+        if rc != 0:
+            msg = self.lib.ttv_last_error().decode(errors="replace")
+            if out.internal:
+                self.lib.ttv_out_free(ctypes.byref(out))
+            raise TTVError(rc, msg)
+        return int(rid.value), (_take_result(self.lib, out) if copy else _view_result(self.lib, out))
 
     def stats(self) -> dict:
         s = Stats()
@@ -1024,6 +1103,7 @@ class Server:
         if self.h:
             self.lib.ttv_server_destroy(self.h)
             self.h = ctypes.c_void_p()
+        _live_servers.discard(self)
 
     def __del__(self):
         try:

@@ -1607,57 +1607,48 @@ struct BatchSortLaunch {
     size_t zero_bytes = 0;
 };
 
-// Builds the job table of the batched problems and uploads it (once, owned
-// by the entry; before the capture starts: the copy is synchronous).
-static int batch_sort_prepare(BatchEntry* e, const std::vector<Plan>& plans, const std::vector<size_t>& ws_off,
-                              const std::vector<int32_t>& batched, char* ws, size_t zero_off, size_t zero_bytes,
-                              ttv_out* outs, BatchSortLaunch& L) {
-    const size_t nb = batched.size();
-    char* zero = ws + zero_off;
-    uint32_t* tickets = reinterpret_cast<uint32_t*>(zero);
-    size_t zo = 256;
-    std::vector<BatchJob> jobs(nb);
-    for (size_t j = 0; j < nb; ++j) {
-        const int32_t i = batched[j];
-        const Plan& pl = plans[(size_t)i];
-        if (!outs[i].subs) return fail(TTV_ERR_ARG, "caller buffers need subs too (problem %d)", i);
-        Arena a;
-        a.base = ws + ws_off[(size_t)i];
-        WsPtrs w;
-        layout(pl, a, w);
-        BatchJob& J = jobs[j];
-        memset(&J, 0, sizeof J);
-        J.p = pl.desc;
-        Status* hs = g_status_pool.acquire();
-        if (!hs) return fail(TTV_ERR_NOMEM, "pinned status allocation failed");
-        e->status[(size_t)i] = hs;
-        memset(hs, 0, sizeof(Status));
-        void* dp = nullptr;
-        cudaError_t ce = cudaHostGetDevicePointer(&dp, hs, 0);
-        if (ce != cudaSuccess || !dp) return cuda_fail(ce, "status mapping");
-        J.p.status = static_cast<Status*>(dp);
-        for (int b = 0; b < 2; ++b) {
-            J.keys[b] = w.sb.keys[b];
-            J.vals[b] = w.sb.vals[b];
-        }
-        J.npass = plan_npass(pl);
-        J.ntiles = sort_tiles(pl.desc.nnz);
-        J.hist = reinterpret_cast<uint32_t*>(zero + zo);
-        zo += round256((size_t)J.npass * 256 * sizeof(uint32_t));
-        J.lookback = reinterpret_cast<uint32_t*>(zero + zo);
-        zo += round256((size_t)J.npass * (size_t)J.ntiles * 256 * sizeof(uint32_t));
-        J.rbk_state = w.rbk_state;
-        const int64_t cap = std::min(outs[i].subs_capacity, outs[i].vals_capacity);
-        J.o = SegOut{outs[i].subs, static_cast<double*>(outs[i].vals), cap, 0, pl.compensated};
-        ttv_out sh{};
-        sh.order = pl.desc.nr;
-        for (int m = 0; m < TTV_MAX_D; ++m) sh.shape[m] = m < pl.desc.nr ? pl.desc.rshape[m] : 0;
-        sh.dtype = TTV_F64;
-        e->shape[(size_t)i] = sh;
-        e->dense_out[(size_t)i] = 0;
+// One batched problem's job: its pair buffers and reduce-by-key state from
+// its own workspace (ws_problem, laid out by layout()), its digit counts and
+// look-back words from the zeroed region (zero + zo, zo advanced), its
+// status block (device address) and result buffers.
+static void fill_batch_job(BatchJob& J, const Plan& pl, char* ws_problem, char* zero, size_t& zo, Status* dstatus,
+                           int64_t* subs, double* vals, int64_t cap_rows) {
+    Arena a;
+    a.base = ws_problem;
+    WsPtrs w;
+    layout(pl, a, w);
+    memset(&J, 0, sizeof J);
+    J.p = pl.desc;
+    J.p.status = dstatus;
+    for (int b = 0; b < 2; ++b) {
+        J.keys[b] = w.sb.keys[b];
+        J.vals[b] = w.sb.vals[b];
     }
-    if (zo != zero_bytes) return fail(TTV_ERR_CUDA, "batch scratch layout mismatch");
+    J.npass = plan_npass(pl);
+    J.ntiles = sort_tiles(pl.desc.nnz);
+    J.hist = reinterpret_cast<uint32_t*>(zero + zo);
+    zo += round256((size_t)J.npass * 256 * sizeof(uint32_t));
+    J.lookback = reinterpret_cast<uint32_t*>(zero + zo);
+    zo += round256((size_t)J.npass * (size_t)J.ntiles * 256 * sizeof(uint32_t));
+    J.rbk_state = w.rbk_state;
+    J.o = SegOut{subs, vals, cap_rows, 0, pl.compensated};
+}
 
+// The job table in host memory: the jobs, then every job list's problem
+// indices and unit prefix, at 256-byte aligned offsets of one blob; launch
+// counts that do not depend on where the blob lands on the device.
+struct BatchTable {
+    struct ListOff { size_t idx, prefix; int32_t count; uint32_t units; };
+    std::vector<char> blob;
+    std::vector<std::pair<int, ListOff>> kt;   // key: d * 4 + layout class
+    ListOff srt{}, rt[2]{}, rg[2]{};
+    int32_t count_per_pass[8] = {0};
+    uint32_t tiles_per_pass[8] = {0};
+    int max_npass = 0;
+};
+
+static void build_batch_table(const std::vector<BatchJob>& jobs, BatchTable& T) {
+    const size_t nb = jobs.size();
     // job lists: one per (order, layout) for the key kernel; all jobs by
     // decreasing pass count for the sort; one per accumulation for the reduction
     struct HostList {
@@ -1668,7 +1659,7 @@ static int batch_sort_prepare(BatchEntry* e, const std::vector<Plan>& plans, con
             prefix.push_back(prefix.back() + (uint32_t)units);
         }
     };
-    std::vector<std::pair<int, HostList>> kt;          // key: d * 4 + layout class
+    std::vector<std::pair<int, HostList>> kt;
     HostList srt, rt[2], rg[2];
     std::vector<int32_t> by_pass(nb);
     for (size_t j = 0; j < nb; ++j) by_pass[j] = (int32_t)j;
@@ -1689,60 +1680,100 @@ static int batch_sort_prepare(BatchEntry* e, const std::vector<Plan>& plans, con
     }
     for (size_t q = 0; q < nb; ++q) {
         const BatchJob& J = jobs[(size_t)by_pass[q]];
-        L.max_npass = std::max(L.max_npass, (int)J.npass);
+        T.max_npass = std::max(T.max_npass, (int)J.npass);
         for (int p = 0; p < J.npass; ++p) {
-            L.count_per_pass[p] = (int32_t)q + 1;
-            L.tiles_per_pass[p] = srt.prefix[q + 1];
+            T.count_per_pass[p] = (int32_t)q + 1;
+            T.tiles_per_pass[p] = srt.prefix[q + 1];
         }
     }
-    // one blob: the jobs, then every list's idx and prefix arrays
-    std::vector<char> blob;
     auto put = [&](const void* src, size_t bytes) {
-        const size_t off = round256(blob.size());
-        blob.resize(off + bytes);
-        if (bytes) memcpy(blob.data() + off, src, bytes);
+        const size_t off = round256(T.blob.size());
+        T.blob.resize(off + bytes);
+        if (bytes) memcpy(T.blob.data() + off, src, bytes);
         return off;
     };
-    struct ListOff { size_t idx, prefix; int32_t count; };
     auto put_list = [&](const HostList& l) {
-        ListOff r;
+        BatchTable::ListOff r;
         r.idx = put(l.idx.data(), l.idx.size() * sizeof(int32_t));
         r.prefix = put(l.prefix.data(), l.prefix.size() * sizeof(uint32_t));
         r.count = (int32_t)l.idx.size();
+        r.units = l.prefix.back();
         return r;
     };
     put(jobs.data(), nb * sizeof(BatchJob));
-    std::vector<ListOff> kt_off;
-    for (auto& c : kt) kt_off.push_back(put_list(c.second));
-    const ListOff srt_off = put_list(srt);
-    ListOff rt_off[2], rg_off[2];
+    for (auto& c : kt) T.kt.emplace_back(c.first, put_list(c.second));
+    T.srt = put_list(srt);
     for (int c = 0; c < 2; ++c) {
-        rt_off[c] = put_list(rt[c]);
-        rg_off[c] = put_list(rg[c]);
+        T.rt[c] = put_list(rt[c]);
+        T.rg[c] = put_list(rg[c]);
     }
-    cudaError_t ce = cudaMalloc(&e->table, std::max<size_t>(blob.size(), 256));
-    if (ce != cudaSuccess) { e->table = nullptr; return cuda_fail(ce, "batch job table"); }
-    ce = cudaMemcpy(e->table, blob.data(), blob.size(), cudaMemcpyHostToDevice);
-    if (ce != cudaSuccess) return cuda_fail(ce, "batch job table");
-    char* tb = static_cast<char*>(e->table);
-    auto dlist = [&](const ListOff& l) {
+}
+
+// The launches of a table copied to device address tb.
+static void bind_batch_table(const BatchTable& T, char* tb, uint32_t* tickets, void* zero, size_t zero_bytes,
+                             BatchSortLaunch& L) {
+    auto dlist = [&](const BatchTable::ListOff& l) {
         return JobList{reinterpret_cast<const int32_t*>(tb + l.idx), reinterpret_cast<const uint32_t*>(tb + l.prefix),
                        l.count};
     };
     L.jobs = reinterpret_cast<const BatchJob*>(tb);
-    for (size_t c = 0; c < kt.size(); ++c)
-        L.kt.push_back(BatchSortLaunch::Kt{dlist(kt_off[c]), kt[c].second.prefix.back(), kt[c].first / 4,
-                                           kt[c].first % 4});
-    L.srt = dlist(srt_off);
+    L.kt.clear();
+    for (const auto& c : T.kt) L.kt.push_back(BatchSortLaunch::Kt{dlist(c.second), c.second.units, c.first / 4, c.first % 4});
+    L.srt = dlist(T.srt);
+    for (int p = 0; p < 8; ++p) {
+        L.count_per_pass[p] = T.count_per_pass[p];
+        L.tiles_per_pass[p] = T.tiles_per_pass[p];
+    }
+    L.max_npass = T.max_npass;
     L.tickets = tickets;
     for (int c = 0; c < 2; ++c) {
-        L.rt[c] = dlist(rt_off[c]);
-        L.rg[c] = dlist(rg_off[c]);
-        L.rtiles[c] = rt[c].prefix.back();
-        L.rgroups[c] = rg[c].prefix.back();
+        L.rt[c] = dlist(T.rt[c]);
+        L.rg[c] = dlist(T.rg[c]);
+        L.rtiles[c] = T.rt[c].units;
+        L.rgroups[c] = T.rg[c].units;
     }
     L.zero = zero;
     L.zero_bytes = zero_bytes;
+}
+
+// Builds the job table of the batched problems and uploads it (once, owned
+// by the entry; before the capture starts: the copy is synchronous).
+static int batch_sort_prepare(BatchEntry* e, const std::vector<Plan>& plans, const std::vector<size_t>& ws_off,
+                              const std::vector<int32_t>& batched, char* ws, size_t zero_off, size_t zero_bytes,
+                              ttv_out* outs, BatchSortLaunch& L) {
+    const size_t nb = batched.size();
+    char* zero = ws + zero_off;
+    size_t zo = 256;              // pass tickets first
+    std::vector<BatchJob> jobs(nb);
+    for (size_t j = 0; j < nb; ++j) {
+        const int32_t i = batched[j];
+        const Plan& pl = plans[(size_t)i];
+        if (!outs[i].subs) return fail(TTV_ERR_ARG, "caller buffers need subs too (problem %d)", i);
+        Status* hs = g_status_pool.acquire();
+        if (!hs) return fail(TTV_ERR_NOMEM, "pinned status allocation failed");
+        e->status[(size_t)i] = hs;
+        memset(hs, 0, sizeof(Status));
+        void* dp = nullptr;
+        cudaError_t ce = cudaHostGetDevicePointer(&dp, hs, 0);
+        if (ce != cudaSuccess || !dp) return cuda_fail(ce, "status mapping");
+        const int64_t cap = std::min(outs[i].subs_capacity, outs[i].vals_capacity);
+        fill_batch_job(jobs[j], pl, ws + ws_off[(size_t)i], zero, zo, static_cast<Status*>(dp), outs[i].subs,
+                       static_cast<double*>(outs[i].vals), cap);
+        ttv_out sh{};
+        sh.order = pl.desc.nr;
+        for (int m = 0; m < TTV_MAX_D; ++m) sh.shape[m] = m < pl.desc.nr ? pl.desc.rshape[m] : 0;
+        sh.dtype = TTV_F64;
+        e->shape[(size_t)i] = sh;
+        e->dense_out[(size_t)i] = 0;
+    }
+    if (zo != zero_bytes) return fail(TTV_ERR_CUDA, "batch scratch layout mismatch");
+    BatchTable T;
+    build_batch_table(jobs, T);
+    cudaError_t ce = cudaMalloc(&e->table, std::max<size_t>(T.blob.size(), 256));
+    if (ce != cudaSuccess) { e->table = nullptr; return cuda_fail(ce, "batch job table"); }
+    ce = cudaMemcpy(e->table, T.blob.data(), T.blob.size(), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) return cuda_fail(ce, "batch job table");
+    bind_batch_table(T, static_cast<char*>(e->table), reinterpret_cast<uint32_t*>(zero), zero, zero_bytes, L);
     e->batched = (int)nb;
     return TTV_OK;
 }
@@ -1755,6 +1786,122 @@ static int batch_sort_issue(const BatchSortLaunch& L, cudaStream_t stream) {
     launch_sort_batch(L.jobs, L.srt, L.count_per_pass, L.tiles_per_pass, L.max_npass, L.tickets, stream);
     for (int c = 0; c < 2; ++c) launch_rbk_batch(L.jobs, L.rt[c], L.rtiles[c], L.rg[c], L.rgroups[c], c == 1, stream);
     return TTV_OK;
+}
+
+// A batch run once, without a graph (the server's groups of requests): the
+// plans, one workspace block and the job table are allocated on the stream,
+// results without caller buffers are library-owned, and every result is
+// finalised by ttv_out_sync and released by ttv_out_free like a single
+// call's.  Problems off the stage-wise sort path run the single-call path on
+// the same stream.  Returns the first failure; results already set up keep
+// their bookkeeping (the caller frees them with ttv_out_free).
+int batch_run_direct(const ttv_problem* probs, int32_t n, ttv_out* outs, const ttv_opts* o, cudaStream_t stream) {
+    if (!probs || !outs || n < 0 || !o) return fail(TTV_ERR_ARG, "bad batch arguments");
+    for (int32_t i = 0; i < n; ++i)
+        if (outs[i].internal) return fail(TTV_ERR_ARG, "ttv_out %d reused without ttv_out_free", i);
+    std::vector<Plan> plans;
+    std::vector<size_t> ws_off;
+    std::vector<int32_t> batched;
+    size_t total = 0, zero_off = 0, zero_bytes = 0;
+    int rc = batch_plans(probs, n, o, plans, ws_off, total, batched, zero_off, zero_bytes);
+    if (rc != TTV_OK) return rc;
+    if (o->path != TTV_PATH_AUTO && o->path != TTV_PATH_SORT) batched.clear();
+    // one workspace per problem, as its single call would take (one block for
+    // a whole group fragments a stream-ordered pool that also serves results),
+    // and the zeroed region of the stage-wise problems
+    std::vector<char*> wsp((size_t)n, nullptr);
+    char* zero = nullptr;
+    auto release = [&]() {
+        for (char* p : wsp)
+            if (p) cudaFreeAsync(p, stream);
+        if (zero) cudaFreeAsync(zero, stream);
+    };
+    cudaError_t ce = cudaSuccess;
+    for (int32_t i = 0; i < n && ce == cudaSuccess; ++i)
+        ce = cudaMallocAsync((void**)&wsp[(size_t)i], std::max<size_t>(workspace_bytes(plans[(size_t)i]), 256), stream);
+    if (ce == cudaSuccess && zero_bytes) ce = cudaMallocAsync((void**)&zero, zero_bytes, stream);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return cuda_fail(ce, "batch workspace");
+    }
+    std::vector<char> on_batch((size_t)n, 0);
+    for (int32_t i : batched) on_batch[(size_t)i] = 1;
+
+    // the stage-wise problems: results, statuses, jobs
+    const size_t nb = batched.size();
+    std::vector<BatchJob> jobs(nb);
+    size_t zo = 256;              // pass tickets first
+    for (size_t j = 0; j < nb && rc == TTV_OK; ++j) {
+        const int32_t i = batched[j];
+        const Plan& pl = plans[(size_t)i];
+        ttv_out* out = &outs[i];
+        OutState* st = new OutState();
+        st->stream = stream;
+        st->auto_fmt = o->fmt == TTV_OUT_AUTO;
+        st->nkeys = pl.desc.nkeys;
+        out->internal = st;
+        out->order = pl.desc.nr;
+        for (int m = 0; m < TTV_MAX_D; ++m) out->shape[m] = m < pl.desc.nr ? pl.desc.rshape[m] : 0;
+        out->dtype = TTV_F64;
+        out->is_dense = 0;
+        out->nnz = 0;
+        st->hstatus = g_status_pool.acquire();
+        if (!st->hstatus) { rc = fail(TTV_ERR_NOMEM, "pinned status allocation failed"); break; }
+        memset(st->hstatus, 0, sizeof(Status));
+        void* dp = nullptr;
+        ce = cudaHostGetDevicePointer(&dp, st->hstatus, 0);
+        if (ce != cudaSuccess || !dp) { rc = cuda_fail(ce, "status mapping"); break; }
+        if (!out->vals) {
+            ce = cudaMallocAsync(&out->vals, (size_t)std::max<int64_t>(pl.cap_vals, 1) * sizeof(double), stream);
+            if (ce != cudaSuccess) { out->vals = nullptr; rc = cuda_fail(ce, "output allocation"); break; }
+            st->owned_vals = out->vals;
+            out->vals_capacity = pl.cap_vals;
+            ce = cudaMallocAsync((void**)&out->subs, (size_t)std::max<int64_t>(pl.cap_rows, 1) * pl.desc.nr * sizeof(int64_t),
+                                 stream);
+            if (ce != cudaSuccess) { out->subs = nullptr; rc = cuda_fail(ce, "output allocation"); break; }
+            st->owned_subs = out->subs;
+            out->subs_capacity = pl.cap_rows;
+        } else if (!out->subs) {
+            rc = fail(TTV_ERR_ARG, "caller buffers need subs too (problem %d)", i);
+            break;
+        }
+        const int64_t cap = std::min(out->subs_capacity, out->vals_capacity);
+        fill_batch_job(jobs[j], pl, wsp[(size_t)i], zero, zo, static_cast<Status*>(dp), out->subs,
+                       static_cast<double*>(out->vals), cap);
+    }
+    char* tb = nullptr;
+    BatchSortLaunch L;
+    if (rc == TTV_OK && nb) {
+        BatchTable T;
+        build_batch_table(jobs, T);
+        ce = cudaMallocAsync((void**)&tb, std::max<size_t>(T.blob.size(), 256), stream);
+        if (ce != cudaSuccess) {
+            tb = nullptr;
+            rc = cuda_fail(ce, "batch job table");
+        } else {
+            // from pageable memory: staged before the call returns, before any
+            // kernel of this batch is queued
+            ce = cudaMemcpyAsync(tb, T.blob.data(), T.blob.size(), cudaMemcpyHostToDevice, stream);
+            if (ce != cudaSuccess) rc = cuda_fail(ce, "batch job table");
+            bind_batch_table(T, tb, reinterpret_cast<uint32_t*>(zero), zero, zero_bytes, L);
+        }
+    }
+    if (rc == TTV_OK && nb) rc = batch_sort_issue(L, stream);
+    // the other problems: the single-call path, on the same stream
+    for (int32_t i = 0; i < n && rc == TTV_OK; ++i) {
+        if (on_batch[(size_t)i]) continue;
+        ttv_opts oi = *o;
+        oi.async = 1;
+        oi.workspace = wsp[(size_t)i];
+        oi.workspace_bytes = workspace_bytes(plans[(size_t)i]);
+        rc = execute(plans[(size_t)i], &outs[i], &oi, stream);
+    }
+    if (tb) cudaFreeAsync(tb, stream);
+    release();
+    ce = cudaGetLastError();
+    if (rc == TTV_OK && ce != cudaSuccess) rc = cuda_fail(ce, "kernel launch");
+    return rc;
 }
 
 static BatchEntry* batch_capture(const ttv_problem* probs, int32_t n, ttv_out* outs, const ttv_opts* o,

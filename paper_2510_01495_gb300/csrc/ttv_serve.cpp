@@ -30,6 +30,7 @@
 namespace ttv {
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
+int batch_run_direct(const ttv_problem* probs, int32_t n, ttv_out* outs, const ttv_opts* o, cudaStream_t stream);
 }  // namespace ttv
 
 namespace {
@@ -63,6 +64,7 @@ struct Request {
     ttv_dtype v_dtype = TTV_F64;
     ttv_opts opts{};
     size_t need = 0;                          // admission estimate (bytes)
+    size_t res_bytes = 0;                     // the result's part of it, held from completion until claimed
     int64_t nnz = 0;
     Clock::time_point submitted;
     // in flight
@@ -75,13 +77,20 @@ struct Request {
     double latency_us = 0;
 };
 
+// A slot runs one request, or a group of requests as one stage-wise batch
+// (ttv::batch_run_direct) when more are queued than slots are free.
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     void* pinned = nullptr;
     size_t pinned_bytes = 0;
     std::shared_ptr<Request> req;
+    std::vector<std::shared_ptr<Request>> group;
+    void* gvecs = nullptr;                    // the group's vectors, one device block
+    bool busy() const { return (bool)req || !group.empty(); }
 };
+
+constexpr size_t kGroupMax = 32;              // requests per group
 
 }  // namespace
 
@@ -98,7 +107,7 @@ struct ttv_server {
     std::vector<Resident> tensors;
     std::vector<double> lat_us;
     uint64_t next_id = 1;
-    long long admitted = 0, refused = 0, completed = 0, prepared_runs = 0;
+    long long admitted = 0, refused = 0, completed = 0, prepared_runs = 0, grouped_runs = 0;
     double nnz_done = 0;
     Clock::time_point t0;
     bool stop = false;
@@ -116,10 +125,8 @@ void free_resident(Resident& r) {
     r.prepared.clear();
 }
 
-// Finishes a request whose slot event has completed.
-void complete(ttv_server* s, Slot& sl) {
-    std::shared_ptr<Request> r = sl.req;
-    sl.req.reset();
+// Finishes one request of a slot whose event has completed.
+void complete_one(ttv_server* s, Slot& sl, const std::shared_ptr<Request>& r) {
     if (r->rc == TTV_OK) {
         r->rc = ttv_out_sync(&r->out);
         if (r->rc != TTV_OK) r->msg = ttv_last_error();
@@ -128,11 +135,12 @@ void complete(ttv_server* s, Slot& sl) {
     if (r->dvecs) cudaFreeAsync(r->dvecs, sl.stream);
     r->latency_us = std::chrono::duration<double, std::micro>(Clock::now() - r->submitted).count();
     std::lock_guard<std::mutex> g(s->mu);
-    // Admission runs ahead of the client's claims (a later, smaller request
-    // may start first), so the budget stops counting a request at completion:
-    // counting unclaimed results could block the very request a client waits
-    // for.  A client should take results as they finish.
+    // From completion until the client claims it, only the result counts
+    // against the budget.  A client waiting by id for a request that the
+    // unclaimed results keep out still progresses: with nothing running, the
+    // oldest queued request is admitted over the budget (the scheduler).
     s->in_use -= r->need;
+    s->in_use += r->res_bytes;
     r->done = true;
     s->running.erase(r->id);
     s->finished[r->id] = r;
@@ -141,6 +149,20 @@ void complete(ttv_server* s, Slot& sl) {
     s->nnz_done += (double)r->nnz;
     s->cv_done.notify_all();
     s->cv_work.notify_all();
+}
+
+void complete(ttv_server* s, Slot& sl) {
+    if (sl.req) {
+        std::shared_ptr<Request> r = sl.req;
+        sl.req.reset();
+        complete_one(s, sl, r);
+        return;
+    }
+    std::vector<std::shared_ptr<Request>> g;
+    g.swap(sl.group);
+    if (sl.gvecs) cudaFreeAsync(sl.gvecs, sl.stream);
+    sl.gvecs = nullptr;
+    for (const auto& r : g) complete_one(s, sl, r);
 }
 
 // Starts a request on a free slot (scheduler thread, lock not held).
@@ -229,6 +251,113 @@ void start(ttv_server* s, Slot& sl, const std::shared_ptr<Request>& r) {
     cudaEventRecord(sl.done, sl.stream);
 }
 
+// Whether a request runs on a prepared layout (the single-request path);
+// called with the server's lock held.
+bool uses_prepared(const ttv_server* s, const Request& r) {
+    if (!((r.opts.accum == TTV_ACCUM_FP64 || r.opts.accum == TTV_ACCUM_COMPENSATED) &&
+          r.opts.path == TTV_PATH_AUTO && !r.opts.deterministic))
+        return false;
+    uint32_t mask = 0;
+    for (int32_t m : r.modes) mask |= 1u << m;
+    for (const auto& pm : s->tensors[(size_t)r.tensor].prepared)
+        if (pm->mask == mask) return true;
+    return false;
+}
+
+// Requests that may share a group: the same options (one batch takes one
+// set) and the same vector type.
+bool same_kind(const Request& a, const Request& b) {
+    return a.opts.fmt == b.opts.fmt && a.opts.path == b.opts.path && a.opts.accum == b.opts.accum &&
+           a.opts.deterministic == b.opts.deterministic && a.v_dtype == b.v_dtype;
+}
+
+// Starts a group of requests on a free slot as one stage-wise batch
+// (scheduler thread, lock not held): their vectors in one upload, then
+// ttv::batch_run_direct on the slot's stream.
+void start_group(ttv_server* s, Slot& sl) {
+    std::vector<std::shared_ptr<Request>>& g = sl.group;
+    const size_t n = g.size();
+    std::vector<Resident> ts(n);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (size_t k = 0; k < n; ++k) ts[k] = s->tensors[(size_t)g[k]->tensor];
+    }
+    for (size_t k = 0; k < n; ++k) g[k]->slot = (int)(&sl - s->slots.data());
+    std::vector<size_t> base(n);
+    size_t vbytes = 0;
+    for (size_t k = 0; k < n; ++k) {
+        base[k] = vbytes;
+        vbytes += (g[k]->vecs.size() + 255) & ~size_t(255);
+    }
+    if (sl.pinned_bytes < vbytes) {
+        if (sl.pinned) cudaFreeHost(sl.pinned);
+        sl.pinned_bytes = std::max<size_t>(vbytes, 1 << 16);
+        if (cudaHostAlloc(&sl.pinned, sl.pinned_bytes, cudaHostAllocDefault) != cudaSuccess) {
+            sl.pinned = nullptr;
+            sl.pinned_bytes = 0;
+        }
+    }
+    cudaError_t e = cudaMallocAsync(&sl.gvecs, std::max<size_t>(vbytes, 256), sl.stream);
+    if (e == cudaSuccess) {
+        if (sl.pinned) {
+            for (size_t k = 0; k < n; ++k) memcpy(static_cast<char*>(sl.pinned) + base[k], g[k]->vecs.data(), g[k]->vecs.size());
+            e = cudaMemcpyAsync(sl.gvecs, sl.pinned, vbytes, cudaMemcpyHostToDevice, sl.stream);
+        } else {
+            for (size_t k = 0; k < n && e == cudaSuccess; ++k)
+                e = cudaMemcpyAsync(static_cast<char*>(sl.gvecs) + base[k], g[k]->vecs.data(), g[k]->vecs.size(),
+                                    cudaMemcpyHostToDevice, sl.stream);
+        }
+    } else {
+        sl.gvecs = nullptr;
+    }
+    int rc = TTV_OK;
+    std::string msg;
+    if (e != cudaSuccess) {
+        rc = ttv::cuda_fail(e, "request vectors");
+        msg = ttv_last_error();
+    } else {
+        std::vector<ttv_problem> probs(n);
+        std::vector<std::vector<const void*>> vps(n);
+        std::vector<ttv_out> outs(n);
+        for (size_t k = 0; k < n; ++k) {
+            const Request& r = *g[k];
+            vps[k].resize(r.modes.size());
+            for (size_t i = 0; i < r.modes.size(); ++i)
+                vps[k][i] = static_cast<char*>(sl.gvecs) + base[k] + r.vec_off[i];
+            ttv_tensor& tt = probs[k].tensor;
+            tt.subs = ts[k].subs;
+            tt.stride_nz = 1;
+            tt.stride_mode = ts[k].nnz;
+            tt.vals = ts[k].vals;
+            tt.val_dtype = ts[k].val_dtype;
+            tt.nnz = ts[k].nnz;
+            tt.shape = ts[k].shape;
+            tt.d = ts[k].d;
+            probs[k].modes = r.modes.data();
+            probs[k].n_v = (int32_t)r.modes.size();
+            probs[k].vecs = vps[k].data();
+            probs[k].v_dtype = r.v_dtype;
+            memset(&outs[k], 0, sizeof outs[k]);
+        }
+        ttv_opts o = g[0]->opts;
+        o.async = 1;
+        o.workspace = nullptr;
+        o.workspace_bytes = 0;
+        rc = ttv::batch_run_direct(probs.data(), (int32_t)n, outs.data(), &o, sl.stream);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->grouped_runs += (long long)n;
+        }
+        if (rc != TTV_OK) msg = ttv_last_error();
+        for (size_t k = 0; k < n; ++k) g[k]->out = outs[k];
+    }
+    for (size_t k = 0; k < n; ++k) {
+        g[k]->rc = rc;
+        g[k]->msg = msg;
+    }
+    cudaEventRecord(sl.done, sl.stream);
+}
+
 void scheduler(ttv_server* s) {
     cudaSetDevice(s->device);
     // While requests run, completions are polled without sleeping (a short
@@ -240,12 +369,21 @@ void scheduler(ttv_server* s) {
     for (;;) {
         // completions (an error state also ends the request: it is reported, never waited on)
         for (Slot& sl : s->slots) {
-            if (!sl.req) continue;
+            if (!sl.busy()) continue;
             const cudaError_t q = cudaEventQuery(sl.done);
             if (q == cudaErrorNotReady) continue;
-            if (q != cudaSuccess && sl.req->rc == TTV_OK) {
-                sl.req->rc = ttv::cuda_fail(q, "request");
-                sl.req->msg = ttv_last_error();
+            if (q != cudaSuccess) {
+                const int rc = ttv::cuda_fail(q, "request");
+                const std::string msg = ttv_last_error();
+                if (sl.req && sl.req->rc == TTV_OK) {
+                    sl.req->rc = rc;
+                    sl.req->msg = msg;
+                }
+                for (auto& r : sl.group)
+                    if (r->rc == TTV_OK) {
+                        r->rc = rc;
+                        r->msg = msg;
+                    }
             }
             complete(s, sl);
             last_event = Clock::now();
@@ -253,34 +391,88 @@ void scheduler(ttv_server* s) {
         std::unique_lock<std::mutex> lk(s->mu);
         if (s->stop && s->queue.empty()) {
             bool busy = false;
-            for (Slot& sl : s->slots) busy |= (bool)sl.req;
+            for (Slot& sl : s->slots) busy |= sl.busy();
             if (!busy) return;
         }
         // admissions: any queued request that fits, in submission order; the
-        // picks are made under the lock, the launches after releasing it
+        // picks are made under the lock, the launches after releasing it.
+        // While no more requests wait than slots are free, each runs on its
+        // own slot; beyond that, a free slot takes a group of requests of the
+        // same kind (up to kGroupMax, about the queue over the free slots),
+        // which runs as one stage-wise batch.
+        size_t nfree = 0;
+        for (Slot& sl : s->slots) nfree += sl.busy() ? 0 : 1;
+        const size_t per_slot =
+            nfree ? std::min<size_t>(kGroupMax, std::max<size_t>(1, (s->queue.size() + nfree - 1) / nfree)) : 1;
         std::vector<std::pair<Slot*, std::shared_ptr<Request>>> picks;
+        std::vector<Slot*> group_picks;
         for (auto it = s->queue.begin(); it != s->queue.end();) {
             Slot* free_slot = nullptr;
             for (Slot& sl : s->slots)
-                if (!sl.req) { free_slot = &sl; break; }
+                if (!sl.busy()) { free_slot = &sl; break; }
             if (!free_slot) break;
             const std::shared_ptr<Request> r = *it;
-            if (s->in_use + r->need > s->budget) { ++it; continue; }
+            if (s->in_use + r->need > s->budget) {
+                bool idle = picks.empty() && group_picks.empty();
+                for (Slot& sl : s->slots) idle = idle && !sl.busy();
+                if (!(idle && it == s->queue.begin())) { ++it; continue; }
+            }
             s->in_use += r->need;
             s->admitted += 1;
             s->running[r->id] = r;
-            free_slot->req = r;              // reserved
-            picks.emplace_back(free_slot, r);
             it = s->queue.erase(it);
+            if (per_slot == 1 || uses_prepared(s, *r)) {
+                free_slot->req = r;              // reserved
+                picks.emplace_back(free_slot, r);
+                continue;
+            }
+            // a group: r and the next admissible requests of its kind (erasing
+            // from the middle of a deque invalidates its iterators: the scan
+            // goes on from the front, where only requests that did not fit
+            // the budget remain before r's successors)
+            // A group holds at most a slot's share of the budget (or its
+            // first request, if that is larger): one slot's group allocates
+            // its workspace as one block, and groups of large requests would
+            // otherwise hold many times the memory of the same requests
+            // running one per slot.
+            free_slot->group.push_back(r);   // reserved
+            const size_t gcap = std::max(r->need, s->budget / s->slots.size());
+            size_t gneed = r->need;
+            for (auto jt = s->queue.begin(); jt != s->queue.end() && free_slot->group.size() < per_slot;) {
+                const std::shared_ptr<Request> q = *jt;
+                if (!same_kind(*r, *q) || uses_prepared(s, *q) || s->in_use + q->need > s->budget ||
+                    gneed + q->need > gcap) {
+                    ++jt;
+                    continue;
+                }
+                gneed += q->need;
+                s->in_use += q->need;
+                s->admitted += 1;
+                s->running[q->id] = q;
+                free_slot->group.push_back(q);
+                jt = s->queue.erase(jt);
+            }
+            it = s->queue.begin();
+            group_picks.push_back(free_slot);
         }
-        const bool started = !picks.empty();
+        const bool started = !picks.empty() || !group_picks.empty();
         if (started) {
             lk.unlock();
             for (auto& pr : picks) start(s, *pr.first, pr.second);
+            for (Slot* sl : group_picks) {
+                if (sl->group.size() == 1) {
+                    // a group of one: the single-request path
+                    std::shared_ptr<Request> r = sl->group[0];
+                    sl->group.clear();
+                    start(s, *sl, r);
+                } else {
+                    start_group(s, *sl);
+                }
+            }
             lk.lock();
         }
         bool any_running = false;
-        for (Slot& sl : s->slots) any_running |= (bool)sl.req;
+        for (Slot& sl : s->slots) any_running |= sl.busy();
         if (started) {
             last_event = Clock::now();
         } else if (any_running) {
@@ -443,7 +635,8 @@ int ttv_server_submit(ttv_server* s, int32_t tensor_id, const int32_t* modes, in
     int rc = ttv_workspace_size(&tt, modes, n_v, v_dtype, &r->opts, &ws);
     if (rc == TTV_OK) rc = ttv_out_capacity(&tt, modes, n_v, &r->opts, &rows, &nvals);
     if (rc != TTV_OK) return rc;
-    r->need = ws + (size_t)rows * (size_t)(t.d - n_v) * 8 + (size_t)nvals * 8 + off;
+    r->res_bytes = (size_t)rows * (size_t)(t.d - n_v) * 8 + (size_t)nvals * 8;
+    r->need = ws + r->res_bytes + off;
     std::lock_guard<std::mutex> g(s->mu);
     size_t resident = 0;
     for (const Resident& x : s->tensors) resident += x.bytes;
@@ -470,10 +663,34 @@ int ttv_server_wait(ttv_server* s, uint64_t req_id, int64_t timeout_us, ttv_out*
     }
     std::shared_ptr<Request> r = s->finished[req_id];
     s->finished.erase(req_id);
+    s->in_use -= r->res_bytes;
+    s->cv_work.notify_all();
     *out = r->out;                       // ownership of the result moves to the caller
     memset(&r->out, 0, sizeof r->out);
     if (r->rc != TTV_OK)
         return ttv::fail(r->rc, "request %llu failed (%d): %s", (unsigned long long)req_id, r->rc, r->msg.c_str());
+    return TTV_OK;
+}
+
+int ttv_server_wait_any(ttv_server* s, int64_t timeout_us, uint64_t* req_id, ttv_out* out) {
+    if (!s || !out || !req_id) return ttv::fail(TTV_ERR_ARG, "bad wait");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto ready = [&] { return !s->finished.empty(); };
+    if (timeout_us < 0) {
+        s->cv_done.wait(lk, ready);
+    } else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
+        return ttv::fail(TTV_ERR_TIMEOUT, "no request finished");
+    }
+    auto it = s->finished.begin();           // the oldest finished request
+    std::shared_ptr<Request> r = it->second;
+    s->finished.erase(it);
+    s->in_use -= r->res_bytes;
+    s->cv_work.notify_all();
+    *req_id = r->id;
+    *out = r->out;                           // ownership of the result moves to the caller
+    memset(&r->out, 0, sizeof r->out);
+    if (r->rc != TTV_OK)
+        return ttv::fail(r->rc, "request %llu failed (%d): %s", (unsigned long long)r->id, r->rc, r->msg.c_str());
     return TTV_OK;
 }
 
@@ -498,6 +715,7 @@ int ttv_server_stats(ttv_server* s, ttv_stats* st) {
     st->bytes_in_use = s->in_use;
     st->budget_bytes = s->budget;
     st->prepared_runs = s->prepared_runs;
+    st->grouped_runs = s->grouped_runs;
     return TTV_OK;
 }
 
@@ -509,6 +727,7 @@ int ttv_server_reset_stats(ttv_server* s) {
     s->admitted = 0;
     s->refused = 0;
     s->prepared_runs = 0;
+    s->grouped_runs = 0;
     s->nnz_done = 0;
     s->t0 = Clock::now();
     return TTV_OK;

@@ -163,3 +163,103 @@ def test_server_prepared_layouts(cuda_lib):
         if modes != [2]:
             assert torch.equal(res.vals, s.vals) and torch.equal(res.subs, s.subs)
     srv.close()
+
+
+@pytest.mark.parametrize("accum", ["fp64", "compensated"])
+def test_server_groups_match_oracle(cuda_lib, accum):
+    """A burst of requests on two slots forms groups that run as stage-wise
+    batches (grouped_runs > 0); every result matches the oracle.  FP64 and
+    FP32-stored tensors are mixed; requests on a prepared layout run alone."""
+    dev = "cuda"
+    g = np.random.default_rng(31)
+    tensors = []
+    for i, (shape, nnz, f32) in enumerate([((300, 200, 100, 50), 150_000, False), ((400, 30, 500, 60), 60_000, True),
+                                           ((1000, 900, 800, 700), 250_000, False), ((40, 50, 60, 70), 30_000, True),
+                                           ((2000, 50, 40, 3000), 5_000, False)]):
+        t = S.sptenrand(600 + i, shape, nnz, vals="u11")
+        v = t.vals.to(torch.float32) if f32 else t.vals
+        tensors.append((t.subs.to(dev), v.to(dev), shape))
+    srv = cuda_lib.Server(budget_bytes=8 << 30, slots=2)
+    ids = [srv.register(s, v, sh) for s, v, sh in tensors]
+    srv.prepare(ids[0], [1])
+    reqs = []
+    for j in range(40):
+        ti = int(g.integers(0, len(tensors)))
+        shape = tensors[ti][2]
+        modes = [1] if (ti == 0 and j % 3 == 0) else [int(m) for m in g.permutation(4)[:1 + j % 2]]
+        vecs = [g.uniform(-1, 1, shape[m]).astype(np.float32 if tensors[ti][1].dtype == torch.float32 else np.float64)
+                for m in modes]
+        reqs.append((ti, modes, vecs))
+    rids = [srv.submit(ids[ti], modes, vecs, accum=accum) for ti, modes, vecs in reqs]
+    results = [srv.wait(r, timeout_us=60_000_000) for r in rids]
+    for k, ((ti, modes, vecs), res) in enumerate(zip(reqs, results)):
+        subs, vals, shape = tensors[ti]
+        ref, A = oracle_ttv(subs, vals.double(), shape, modes, [v.astype(np.float64) for v in vecs])
+        check_result(res, ref, A, what=f"request {k}")
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["pending"] == 0
+    assert st["grouped_runs"] > 0, st
+    srv.close()
+
+
+def test_server_wait_any_completion_order(cuda_lib):
+    """wait_any hands out every finished request exactly once, whatever the
+    order they finish in, each with its own result."""
+    dev = "cuda"
+    g = np.random.default_rng(37)
+    t_big = S.sptenrand(700, (1000, 800, 600, 400), 600_000, vals="u11")
+    t_small = S.sptenrand(701, (30, 40, 50, 60), 2_000, vals="u11")
+    tensors = [(t_big.subs.to(dev), t_big.vals.to(dev), t_big.shape),
+               (t_small.subs.to(dev), t_small.vals.to(dev), t_small.shape)]
+    srv = cuda_lib.Server(budget_bytes=8 << 30, slots=2)
+    ids = [srv.register(s, v, sh) for s, v, sh in tensors]
+    resident = srv.stats()["bytes_in_use"]
+    reqs = {}
+    for j in range(16):
+        ti = 0 if j % 8 == 0 else 1
+        m = int(g.integers(0, 4))
+        x = g.uniform(-1, 1, tensors[ti][2][m])
+        reqs[srv.submit(ids[ti], [m], [x])] = (ti, m, x)
+    got = {}
+    for k in range(len(reqs)):
+        rid, res = srv.wait_any(timeout_us=60_000_000, copy=bool(k % 2))   # views and copies
+        assert rid in reqs and rid not in got
+        got[rid] = res
+    # every result claimed: only the resident tensors hold budget
+    assert srv.stats()["bytes_in_use"] == resident
+    with pytest.raises(cuda_lib.TTVError) as e:
+        srv.wait_any(timeout_us=1000)
+    assert e.value.name == "TTV_ERR_TIMEOUT"
+    for rid, (ti, m, x) in reqs.items():
+        subs, vals, shape = tensors[ti]
+        ref, A = oracle_ttv(subs, vals, shape, [m], [x])
+        check_result(got[rid], ref, A, what=f"request {rid}")
+    srv.close()
+
+
+def test_server_unclaimed_results_hold_budget_without_deadlock(cuda_lib):
+    """Unclaimed results count against the budget; a client that waits by id
+    for the last request while earlier results sit unclaimed still gets it
+    (with nothing running, the oldest queued request is admitted)."""
+    dev = "cuda"
+    t = S.sptenrand(710, (400, 300, 500, 200), 300_000, vals="u11")
+    subs, vals = t.subs.to(dev), t.vals.to(dev)
+    probe = cuda_lib.Server(budget_bytes=8 << 30, slots=1)
+    probe.register(subs, vals, t.shape)
+    resident = probe.stats()["bytes_in_use"]
+    probe.close()
+    ws = cuda_lib.workspace_size(subs, vals, t.shape, [1])
+    rows, nv = cuda_lib.out_capacity(subs, vals, t.shape, [1])
+    need = ws + rows * 3 * 8 + nv * 8 + 4096
+    srv = cuda_lib.Server(budget_bytes=resident + int(1.2 * need), slots=2)
+    tid = srv.register(subs, vals, t.shape)
+    g = np.random.default_rng(41)
+    xs = [g.uniform(-1, 1, t.shape[1]) for _ in range(4)]
+    rids = [srv.submit(tid, [1], [x]) for x in xs]
+    for rid, x in reversed(list(zip(rids, xs))):
+        res = srv.wait(rid, timeout_us=60_000_000)
+        ref, A = oracle_ttv(subs, vals, t.shape, [1], [x])
+        check_result(res, ref, A)
+    st = srv.stats()
+    assert st["completed"] == 4 and st["bytes_in_use"] == resident
+    srv.close()
