@@ -866,12 +866,14 @@ def run_serve(args, rank, world, local_rank):
 
     rows = []   # result rows of each request of the last stream, in submission order
 
-    def stream(accum, arr=None, items=None):
+    def stream(accum, arr=None, items=None, server=None, tids=None):
         # the client takes every result as soon as it is ready (a waiter
         # thread, in submission order), so results do not pile up on the device
         import queue
         arr = arrivals if arr is None else arr
         items = reqs[64:] if items is None else items
+        server = srv if server is None else server
+        tids = ids if tids is None else tids
         pending = queue.Queue()
         errors = []
         rows.clear()
@@ -886,7 +888,7 @@ def run_serve(args, rank, world, local_rank):
                 if rid is None:
                     return
                 try:
-                    got, res = srv.wait_any(timeout_us=120_000_000, copy=False)
+                    got, res = server.wait_any(timeout_us=120_000_000, copy=False)
                     rid_rows[got] = int(res.vals.numel())
                 except Exception as e:   # noqa: BLE001 -- re-raised by the submitting thread
                     errors.append(e)
@@ -899,7 +901,7 @@ def run_serve(args, rank, world, local_rank):
             delay = arr[k] - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            rid = srv.submit(ids[ti], [m], [x], accum=accum)
+            rid = server.submit(tids[ti], [m], [x], accum=accum)
             rids.append(rid)
             pending.put(rid)
         pending.put(None)
@@ -925,8 +927,12 @@ def run_serve(args, rank, world, local_rank):
     light_arr = np.cumsum(g.exponential(1.0 / args.light_rate, size=n_light))
     stream("compensated", light_arr, reqs[64:64 + n_light])
     st_l = srv.stats()
-    # the plain form on the same requests, right after (the same state of the
-    # GPU and its memory pool): one request at a time, submit then wait
+    # the one-slot server on the same paced requests, right after: the same
+    # client, the same state of the GPU and its memory pool
+    plain.reset_stats()
+    stream("compensated", light_arr, reqs[64:64 + n_light], server=plain, tids=pids)
+    pst_l = plain.stats()
+    # the plain form's throughput: one request at a time, submit then wait
     n_plain = min(300, args.requests)
     plain.reset_stats()
     t1 = time.perf_counter()
@@ -997,7 +1003,10 @@ def run_serve(args, rank, world, local_rank):
                            "accum": "compensated (prepared runs)"},
         "plain": {"requests": n_plain, "throughput_rps": n_plain / wall_plain,
                   "throughput_gnnz_s": plain_nnz / wall_plain / 1e9, "p50_ms": pst["p50_us"] / 1e3,
-                  "p99_ms": pst["p99_us"] / 1e3},
+                  "p99_ms": pst["p99_us"] / 1e3, "note": "one slot, submit then wait"},
+        "plain_light": {"rate_req_s": args.light_rate, "requests": n_light, "p50_ms": pst_l["p50_us"] / 1e3,
+                        "p99_ms": pst_l["p99_us"] / 1e3,
+                        "note": "one-slot server, the light-load stream above (same arrivals, same client)"},
         "clocks": clk, "accuracy_fp32_storage": accuracy,
     }
     peaks, peak_src = load_peaks()

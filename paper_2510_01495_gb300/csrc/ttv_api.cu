@@ -897,6 +897,19 @@ void ttv_out_free(ttv_out* out) {
     out->internal = nullptr;
 }
 
+}  // extern "C"
+
+namespace ttv {
+// A result whose stream may be destroyed before the result is released (a
+// server's slot streams): once its work has completed, its later release
+// and synchronisation run on the legacy default stream instead.
+void out_detach_stream(ttv_out* out) {
+    if (out && out->internal) static_cast<OutState*>(out->internal)->stream = nullptr;
+}
+}  // namespace ttv
+
+extern "C" {
+
 void ttv_outs_free(ttv_out* outs, int32_t n) {
     if (!outs) return;
     for (int32_t i = 0; i < n; ++i) ttv_out_free(&outs[i]);

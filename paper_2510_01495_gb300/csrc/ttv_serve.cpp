@@ -31,6 +31,7 @@ namespace ttv {
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 int batch_run_direct(const ttv_problem* probs, int32_t n, ttv_out* outs, const ttv_opts* o, cudaStream_t stream);
+void out_detach_stream(ttv_out* out);
 }  // namespace ttv
 
 namespace {
@@ -131,6 +132,9 @@ void complete_one(ttv_server* s, Slot& sl, const std::shared_ptr<Request>& r) {
         r->rc = ttv_out_sync(&r->out);
         if (r->rc != TTV_OK) r->msg = ttv_last_error();
     }
+    // the slot's work for this result is complete (its event): the client may
+    // release the result after the server, and so the slot stream, are gone
+    ttv::out_detach_stream(&r->out);
     // the result now belongs to the client: its buffers must not be touched here
     if (r->dvecs) cudaFreeAsync(r->dvecs, sl.stream);
     r->latency_us = std::chrono::duration<double, std::micro>(Clock::now() - r->submitted).count();
