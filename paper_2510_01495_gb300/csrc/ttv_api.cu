@@ -1651,7 +1651,7 @@ static void fill_batch_job(BatchJob& J, const Plan& pl, char* ws_problem, char* 
 // indices and unit prefix, at 256-byte aligned offsets of one blob; launch
 // counts that do not depend on where the blob lands on the device.
 struct BatchTable {
-    struct ListOff { size_t idx, prefix; int32_t count; uint32_t units; };
+    struct ListOff { size_t idx, prefix; int32_t count; uint32_t units; size_t unit_pos = 0; bool has_map = false; };
     std::vector<char> blob;
     std::vector<std::pair<int, ListOff>> kt;   // key: d * 4 + layout class
     ListOff srt{}, rt[2]{}, rg[2]{};
@@ -1705,20 +1705,29 @@ static void build_batch_table(const std::vector<BatchJob>& jobs, BatchTable& T) 
         if (bytes) memcpy(T.blob.data() + off, src, bytes);
         return off;
     };
-    auto put_list = [&](const HostList& l) {
+    // map: the list's position of every unit, for the kernels whose CTAs are
+    // short (a tile each), so that finding the problem is one load
+    auto put_list = [&](const HostList& l, bool map) {
         BatchTable::ListOff r;
         r.idx = put(l.idx.data(), l.idx.size() * sizeof(int32_t));
         r.prefix = put(l.prefix.data(), l.prefix.size() * sizeof(uint32_t));
         r.count = (int32_t)l.idx.size();
         r.units = l.prefix.back();
+        if (map && r.units) {
+            std::vector<uint32_t> pos(r.units);
+            for (size_t q = 0; q < l.idx.size(); ++q)
+                for (uint32_t u = l.prefix[q]; u < l.prefix[q + 1]; ++u) pos[u] = (uint32_t)q;
+            r.unit_pos = put(pos.data(), pos.size() * sizeof(uint32_t));
+            r.has_map = true;
+        }
         return r;
     };
     put(jobs.data(), nb * sizeof(BatchJob));
-    for (auto& c : kt) T.kt.emplace_back(c.first, put_list(c.second));
-    T.srt = put_list(srt);
+    for (auto& c : kt) T.kt.emplace_back(c.first, put_list(c.second, false));
+    T.srt = put_list(srt, true);
     for (int c = 0; c < 2; ++c) {
-        T.rt[c] = put_list(rt[c]);
-        T.rg[c] = put_list(rg[c]);
+        T.rt[c] = put_list(rt[c], true);
+        T.rg[c] = put_list(rg[c], false);
     }
 }
 
@@ -1727,7 +1736,7 @@ static void bind_batch_table(const BatchTable& T, char* tb, uint32_t* tickets, v
                              BatchSortLaunch& L) {
     auto dlist = [&](const BatchTable::ListOff& l) {
         return JobList{reinterpret_cast<const int32_t*>(tb + l.idx), reinterpret_cast<const uint32_t*>(tb + l.prefix),
-                       l.count};
+                       l.count, l.has_map ? reinterpret_cast<const uint32_t*>(tb + l.unit_pos) : nullptr};
     };
     L.jobs = reinterpret_cast<const BatchJob*>(tb);
     L.kt.clear();

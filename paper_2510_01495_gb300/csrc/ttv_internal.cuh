@@ -419,6 +419,7 @@ struct JobList {
     const int32_t* idx;
     const uint32_t* prefix;
     int32_t count;
+    const uint32_t* unit_pos = nullptr;   // position in the list of every unit (nullptr: search prefix)
 };
 
 constexpr int64_t kKtBatchChunk = 16384;   // nonzeros per CTA of the batched key kernel

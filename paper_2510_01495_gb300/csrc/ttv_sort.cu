@@ -320,6 +320,12 @@ __device__ __forceinline__ int job_of(const uint32_t* __restrict__ prefix, int c
     return lo;
 }
 
+// The position in job list l of the problem unit t belongs to: one load from
+// the list's unit map when it has one, else a binary search of its prefix.
+__device__ __forceinline__ int job_at(const JobList& l, uint32_t t) {
+    return l.unit_pos ? (int)__ldg(l.unit_pos + t) : job_of(l.prefix, l.count, t);
+}
+
 // One digit pass over the tiles of every problem of a batch with more than
 // `pass` digits (the list's first l.count problems).  CTAs take global
 // tickets, problem after problem, so each problem's tiles are claimed in
@@ -333,7 +339,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep_batch(const BatchJ
     if (tid == 0) {
         const uint32_t t = atomicAdd(ticket, 1u);
         sm.tile = t;
-        s_pos = t < __ldg(l.prefix + l.count) ? job_of(l.prefix, l.count, t) : -1;
+        s_pos = t < __ldg(l.prefix + l.count) ? job_at(l, t) : -1;
     }
     for (int i = tid; i < kSortWarps * kHistStride; i += kSortThreads) sm.whist[i] = 0;
     __syncthreads();
@@ -1262,7 +1268,7 @@ __device__ __forceinline__ const double* job_vals(const BatchJob& J) { return J.
 template <bool kComp>
 __global__ void __launch_bounds__(kRbkThreads) k_rbk_tiles_batch(const BatchJob* __restrict__ jobs, JobList l) {
     __shared__ int s_pos;
-    if (threadIdx.x == 0) s_pos = job_of(l.prefix, l.count, blockIdx.x);
+    if (threadIdx.x == 0) s_pos = job_at(l, blockIdx.x);
     __syncthreads();
     const int pos = s_pos;
     const BatchJob& J = jobs[__ldg(l.idx + pos)];
@@ -1297,7 +1303,7 @@ __global__ void __launch_bounds__(kRbkThreads, rbk_emit_ctas<KeyHeads>()) k_rbk_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RbkEmitSmem& sm = *reinterpret_cast<RbkEmitSmem*>(smem_raw);
     __shared__ int s_pos;
-    if (threadIdx.x == 0) s_pos = job_of(l.prefix, l.count, blockIdx.x);
+    if (threadIdx.x == 0) s_pos = job_at(l, blockIdx.x);
     __syncthreads();
     const int pos = s_pos;
     const BatchJob& J = jobs[__ldg(l.idx + pos)];
