@@ -1069,17 +1069,22 @@ __device__ __forceinline__ void rbk_emit_body(RbkEmitSmem& sm, const H& hd, cons
                                               const unsigned long long* __restrict__ gheads, const StreamDesc& p,
                                               const SegOut& o, Status* st) {
     const int64_t ntiles = (n + kRbkTile - 1) / kRbkTile;
+    // the tile's carries first: they do not depend on its pairs, and loaded
+    // after the block scan's barriers they would add an L2 round trip
+    const int64_t g = tile / kRbkGroup;
+    const RbkSum ig = ingroup[tile];
+    const double gp_val = gprefix[g].val;
+    const double gp_comp = kComp ? gprefix[g].comp : 0.0;
+    const unsigned long long gh = gheads[g];
     RbkPairs r;
     rbk_load<kComp>(hd, src, n, tile, r);
     uint32_t xc, xf, tc, tf;
     double xv, xk, tv, tk;
     rbk_block_scan<kComp>(r, sm.ss, xc, xf, xv, xk, tc, tf, tv, tk);
     // open value entering the tile: group prefix . in-group prefix
-    const RbkSum ig = ingroup[tile];
-    const int64_t g = tile / kRbkGroup;
     double carry = ig.val, carry_k = kComp ? ig.comp : 0.0;
-    if (!ig.flag) cat_sum<kComp>(gprefix[g].val, kComp ? gprefix[g].comp : 0.0, carry, carry_k);
-    const unsigned long long hb = gheads[g] + ig.cnt;
+    if (!ig.flag) cat_sum<kComp>(gp_val, gp_comp, carry, carry_k);
+    const unsigned long long hb = gh + ig.cnt;
     // value of the run open when this thread's range starts
     double base = xv, base_k = xk;
     if (!xf) cat_sum<kComp>(carry, carry_k, base, base_k);
