@@ -47,3 +47,40 @@ def test_sptensor_arrays_of_sparse_and_dense_results():
     s, v, shp = ttv.Result(None, dense, (3, 2), True).to_sptensor_arrays()
     # the nonzero cells, in row-major (pyttb unique) order, values as a column
     assert s.tolist() == [[0, 1], [2, 0]] and v.tolist() == [[1.5], [-2.0]] and shp == (3, 2)
+
+
+def test_out_structured_view_matches_the_c_struct():
+    """The binding reads every batch result's size, order, shape and format in
+    one pass over the ttv_out array through a numpy view: the view's fields
+    must sit where the ctypes struct (the C layout) has them."""
+    import ctypes
+    import numpy as np
+    from paper_2510_01495_gb300 import Out, _OUT_DTYPE, TTV_MAX_D
+    assert _OUT_DTYPE.itemsize == ctypes.sizeof(Out)
+    arr = (Out * 3)()
+    arr[1].nnz, arr[1].is_dense, arr[1].order = 77, 1, 2
+    arr[1].shape[0], arr[1].shape[1] = 5, 6
+    arr[2].nnz, arr[2].order, arr[2].shape[TTV_MAX_D - 1] = -1, TTV_MAX_D, 9
+    a = np.frombuffer(arr, dtype=_OUT_DTYPE, count=3)
+    assert a["nnz"].tolist() == [0, 77, -1]
+    assert a["is_dense"].tolist() == [0, 1, 0]
+    assert a["order"].tolist() == [0, 2, TTV_MAX_D]
+    assert a["shape"][1].tolist()[:2] == [5, 6] and a["shape"][2].tolist()[-1] == 9
+
+
+def test_batch_results_are_formed_on_access():
+    """BatchResults: a view per problem of the batch's buffers, sized by the
+    run's result count; sparse rows and dense arrays; slices and iteration."""
+    import torch
+    from paper_2510_01495_gb300 import BatchResults
+    ov0, os0 = torch.arange(10, dtype=torch.float64), torch.arange(20, dtype=torch.int64).view(10, 2)
+    ov1 = torch.arange(6, dtype=torch.float64)
+    meta = [(ov0, os0, (4, 4), [0]), (ov1, None, (2, 3), [1])]
+    info = [(3, False, 2, (4, 4, 0, 0, 0, 0, 0, 0)), (6, True, 2, (2, 3, 0, 0, 0, 0, 0, 0))]
+    res = BatchResults(meta, info)
+    assert len(res) == 2
+    r0, r1 = res
+    assert not r0.is_dense and r0.shape == (4, 4) and r0.vals.tolist() == [0.0, 1.0, 2.0]
+    assert r0.subs.tolist() == [[0, 1], [2, 3], [4, 5]]
+    assert r1.is_dense and r1.subs is None and tuple(r1.vals.shape) == (2, 3)
+    assert [r.shape for r in res[0:2]] == [(4, 4), (2, 3)]
