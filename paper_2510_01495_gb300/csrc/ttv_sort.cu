@@ -161,17 +161,19 @@ __device__ __forceinline__ void onesweep_tile(OnesweepSmem& sm, const uint64_t* 
     }
     // Warp-level multi-split: rank of each item among equal digits of its
     // warp.  The lanes holding the same digit are found by one ballot per
-    // digit bit (nine: the digit and the padding bucket), measured faster
-    // than __match_any_sync here.
+    // digit bit, measured faster than __match_any_sync here; a ninth ballot
+    // (the padding bucket of absent items) only in the last, partial tile
+    // (8.35 against 8.66 ms for the 1e8 Zipf TTV with nine everywhere).
     uint32_t* wh = sm.whist + warp * kHistStride;
     const uint32_t lt = lanemask_lt();
+    const bool full_tile = base + kSortTile <= n;
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
         // padding bucket kRadix for absent items: never published or written
         const uint32_t dig = wbase + i * 32 < n ? (uint32_t)(k[i] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
         uint32_t mask = 0xffffffffu;
 #pragma unroll
-        for (int b = 0; b <= kRadixBits; ++b) {
+        for (int b = 0; b < kRadixBits + (full_tile ? 0 : 1); ++b) {
             const uint32_t bit = (dig >> b) & 1u;
             const uint32_t bal = __ballot_sync(0xffffffffu, bit);
             mask &= bit ? bal : ~bal;
