@@ -1071,18 +1071,34 @@ __device__ __forceinline__ void rbk_emit_body(RbkEmitSmem& sm, const H& hd, cons
                                               const unsigned long long* __restrict__ gheads, const StreamDesc& p,
                                               const SegOut& o, Status* st) {
     const int64_t ntiles = (n + kRbkTile - 1) / kRbkTile;
-    // the tile's carries first: they do not depend on its pairs, and loaded
-    // after the block scan's barriers they would add an L2 round trip
+    // Sorted pairs (4 CTAs per SM, 64 registers): the tile's carries are
+    // loaded first, since they do not depend on its pairs and loaded after
+    // the block scan's barriers they add an L2 round trip (0.97 against
+    // 1.04 ms per 1e8 pairs).  Prepared runs (5 CTAs per SM, 48 registers)
+    // load them after the scan: holding them across it cost more there
+    // (1.42 against 1.26 ms).
+    constexpr bool kEarly = !H::kBits;
     const int64_t g = tile / kRbkGroup;
-    const RbkSum ig = ingroup[tile];
-    const double gp_val = gprefix[g].val;
-    const double gp_comp = kComp ? gprefix[g].comp : 0.0;
-    const unsigned long long gh = gheads[g];
+    RbkSum ig{0.0, 0.0, 0u, 0u};
+    double gp_val = 0.0, gp_comp = 0.0;
+    unsigned long long gh = 0;
+    if constexpr (kEarly) {
+        ig = ingroup[tile];
+        gp_val = gprefix[g].val;
+        gp_comp = kComp ? gprefix[g].comp : 0.0;
+        gh = gheads[g];
+    }
     RbkPairs r;
     rbk_load<kComp>(hd, src, n, tile, r);
     uint32_t xc, xf, tc, tf;
     double xv, xk, tv, tk;
     rbk_block_scan<kComp>(r, sm.ss, xc, xf, xv, xk, tc, tf, tv, tk);
+    if constexpr (!kEarly) {
+        ig = ingroup[tile];
+        gp_val = gprefix[g].val;
+        gp_comp = kComp ? gprefix[g].comp : 0.0;
+        gh = gheads[g];
+    }
     // open value entering the tile: group prefix . in-group prefix
     double carry = ig.val, carry_k = kComp ? ig.comp : 0.0;
     if (!ig.flag) cat_sum<kComp>(gp_val, gp_comp, carry, carry_k);
