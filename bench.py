@@ -106,13 +106,13 @@ DOMINANT = {"allbutone_4way_1000": [("dense_accum", _stream_bytes), ("dense_fx",
 STEP_TRAFFIC = {
     "batch_512": {
         "files": ["ttv_keys.cu", "ttv_sort.cu", "ttv_internal.cuh", "ttv_udiv.h"],
-        "sha": "7553294072d7",
-        "bytes_per_step": 43758844160,   # the 19 stage-wise launches of one step; 4.14x the algorithmic bytes
+        "sha": "4c23fb15fea3",
+        "bytes_per_step": 43772273664,   # the 19 stage-wise launches of one step; 4.14x the algorithmic bytes
     },
     "single_5way_zipf": {
         "files": ["ttv_keys.cu", "ttv_sort.cu", "ttv_internal.cuh", "ttv_udiv.h"],
-        "sha": "7553294072d7",
-        "bytes_per_step": 31008289024,   # 12 launches of one (warm) TTV; 4.3x the algorithmic bytes
+        "sha": "4c23fb15fea3",
+        "bytes_per_step": 31025177088,   # 12 launches of one (warm) TTV; 4.3x the algorithmic bytes
     },
 }
 
